@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Benchmark of the per-iteration deformation-grid optimisation step (Preconditioned
+Deformation Grids, arXiv 2509.18097) on one GB300 per rank.
+
+Workload (headline): frame pair on the ellipsoid (1, 0.7, 0.5): 50 412-vertex geodesic
+template (151 230 edges), 100 000 source and 100 000 target points (target deformed by
+0.05 [sin 2pi y, sin 2pi z, sin 2pi x]), displacement grids 16^3, 32^3, 64^3, 128^3 over
+[-1.5, 1.5]^3, zero-initialised.  Synthetic, seeded (see paper_2509_18097_gb300.synth).
+
+A "step" is one optimisation iteration: trilinear evaluation, the four exact nearest-
+neighbour searches of the bidirectional robust Chamfer distance with its gradient, the
+isometry term, the adjoint into the grids, the Sobolev preconditioner and Adam.
+
+value: steps/s, device-timed with CUDA events around each step (one CUDA-graph replay),
+L2 flushed (256 MiB write) between steps outside the events.  e2e: the same metric through
+pdg_fit_frame with HOST buffers (pinned target in, vertices + stats out) in the timed
+region.  Multi-GPU: independent replicas (one sequence per rank), no collective on the
+data path; value = steps of all ranks / max time.
+
+--impl reference times the FP64 CPU oracle on the same workload (bounded sample).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "opt steps/s @100k pts x4 grid levels"
+WORKLOAD = "ellipsoid_pair_100k: 50412-vert template, 100k src + 100k tgt pts, grids 16^3/32^3/64^3/128^3"
+STEPS_PER_FRAME_E2E = 100
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+# ------------------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        if len({r[0].strip() for r in rows}) > 1:  # several GPUs visible: keep this rank's
+            rows = [r for r in rows if r[0].strip() == str(self.index)]
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------ helpers
+
+
+def candidate_flops(y, V, target, bits, lo=-1.5, hi=1.5):
+    """Distance evaluations of the one-ring search (8 flops each): for every query the
+    number of points in its 3x3x3 cell box, computed from the same cell grids."""
+    import numpy as np
+
+    G = 1 << bits
+
+    def cells(p):
+        c = np.floor((p - lo) * (G / (hi - lo))).astype(np.int64)
+        return np.clip(c, 0, G - 1)
+
+    def box_counts(pts):
+        c = cells(pts)
+        h = np.zeros((G + 2, G + 2, G + 2), np.int64)
+        np.add.at(h, (c[:, 2] + 1, c[:, 1] + 1, c[:, 0] + 1), 1)
+        b = np.zeros_like(h)
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    b += np.roll(np.roll(np.roll(h, dz, 0), dy, 1), dx, 2)
+        return b
+
+    def lookup(b, q):
+        c = cells(q)
+        return b[c[:, 2] + 1, c[:, 1] + 1, c[:, 0] + 1].sum()
+
+    bt = box_counts(target)
+    n = lookup(bt, y)  # forward: template + source into the target
+    n += lookup(box_counts(y[:V]), target) + lookup(box_counts(y[V:]), target)
+    return 8.0 * float(n)
+
+
+def grid_bits(count):
+    import math
+
+    g = math.sqrt(max(count, 1) / 8.0)
+    return min(max(int(round(math.log2(max(g, 1.0)))), 2), 7)
+
+
+def active_vertices(x, res, lo=-1.5, hi=1.5):
+    import numpy as np
+
+    out = []
+    for n in res:
+        if n == 1:
+            out.append(1)
+            continue
+        u = np.clip((x - lo) / (hi - lo) * (n - 1), 0, n - 1)
+        i0 = np.minimum(np.floor(u), n - 2).astype(np.int64)
+        vs = []
+        for dz in (0, 1):
+            for dy in (0, 1):
+                for dx in (0, 1):
+                    vs.append(((i0[:, 2] + dz) * n + i0[:, 1] + dy) * n + i0[:, 0] + dx)
+        out.append(len(np.unique(np.concatenate(vs))))
+    return out
+
+
+def stage_model(stage, Q, V, M, E, res, act):
+    """Algorithmic work of one launch of a stage: (bound, amount, unit).  Bytes count the
+    data the operation must move once (12 B per point or grid value, 4 B per scalar)."""
+    G = sum(n**3 for n in res)
+    A = sum(act)
+    if stage == "sobolev":  # read g, read+write theta, m, v (Eq. 3 + Adam)
+        return "hbm", G * (12 + 3 * 24), "B"
+    if stage == "interp":  # read x, write y, read each touched grid value
+        return "hbm", Q * 24 + A * 12, "B"
+    if stage == "adjoint":  # read x and dL/dy, write each touched grid gradient
+        return "hbm", Q * 24 + A * 12, "B"
+    if stage in ("nn", "nn_hard"):
+        return "alu", None, "FLOP"
+    if stage == "iso_edges":
+        return "hbm", E * (8 + 4 + 4 + 12) + V * 12, "B"
+    if stage == "assemble":
+        return "hbm", Q * (12 + 12 + 12) + V * 12, "B"
+    if stage == "loss":
+        return "hbm", (Q + 2 * M + E) * 4, "B"
+    if stage == "mov_scan":
+        G3 = 2 * (1 << (3 * grid_bits(max(V, M))))
+        return "hbm", G3 * 8, "B"
+    if stage == "mov_scatter":
+        return "hbm", Q * (4 + 12 + 16), "B"
+    return "hbm", 0, "B"
+
+
+# ------------------------------------------------------------------------------ reference arm
+
+
+def run_reference(args, world, rank):
+    import numpy as np
+
+    from oracle import pdg_oracle as O
+    from paper_2509_18097_gb300 import synth
+
+    if rank != 0:
+        return
+    w = synth.ellipsoid_pair(seed=0, theta_sigma=0)
+    cfg = O.Config(res=w.res)
+    n = max(1, min(args.steps, 2))
+    st = O.begin_frame(w.template, w.source, w.target, w.edges, cfg)
+    t0 = time.perf_counter()
+    for _ in range(n):
+        O.step(st, cfg)
+    dt = time.perf_counter() - t0
+    v = n / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": world,
+            "steps": n, "warmup": 0, "ms_per_step": 1000 * dt / n, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{n} full oracle steps of the headline workload (numpy FP64, single thread)"},
+            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------ GPU arm
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=10)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    __graft_entry__.build()
+    from paper_2509_18097_gb300 import binding as B
+    from paper_2509_18097_gb300 import synth
+
+    w = synth.ellipsoid_pair(seed=0, theta_sigma=0)
+    V, N, M, E = len(w.template), len(w.source), len(w.target), len(w.edges)
+    Q = V + N
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    cfg = B.pdg_config_default(res=w.res)
+    ctx = B.pdg_create(cfg, T(w.template), T(w.edges), T(w.source), max_pts=max(N, M))
+    tgt_dev = T(w.target)
+    B.pdg_begin_frame(ctx, tgt_dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    B.pdg_step(ctx, args.warmup)
+    torch.cuda.synchronize()
+    flush_buf = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush_buf.fill_(i & 0xFF)  # 256 MiB write evicts the 129 MB L2
+            ev0[i].record(stream)
+            B.pdg_step(ctx, 1)
+            ev1[i].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        wall = time.perf_counter() - wall0
+        # steady state, resident in L2 (extra information, not the headline)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        B.pdg_step(ctx, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    clocks = clk.summary()
+    dev_ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+    resident_ms = e0.elapsed_time(e1) / args.steps
+    t_max = dev_ms
+    if dist is not None:
+        tt = torch.tensor([dev_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * args.steps / (t_max / 1000.0)
+    ms_per_step = t_max / args.steps
+
+    # per-stage profile (eager launches of the same stages, events per stage)
+    prof = B.pdg_profile_step(ctx, args.profile_steps)
+    prof = {k: v / args.profile_steps for k, v in prof.items()}
+    y = B.pdg_read(ctx, B.BUF_Y, 0, np.empty((Q, 3), np.float32)).astype(np.float64)
+    B.pdg_end_frame(ctx)
+    act = active_vertices(np.concatenate([w.template, w.source]).astype(np.float64), w.res)
+    hbm_peak, sm_max, peak_kind = load_peaks()
+    sm_mhz = clocks["sm_mhz"] or sm_max
+    dom = max(prof, key=prof.get)
+    bound, amount, unit = stage_model(dom, Q, V, M, E, w.res, act)
+    if bound == "alu":
+        amount = candidate_flops(y, V, w.target.astype(np.float64), grid_bits(M))
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+        achieved = amount / (prof[dom] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": dom, "peak_note": f"FP32 {sms} SMs x 128 FMA x 2 at {sm_mhz:.0f} MHz"}
+    else:
+        achieved = amount / (prof[dom] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": None, "kernel": dom, "peak_note": f"{peak_kind} copy bandwidth"}
+    stages = {}
+    for k, ms in prof.items():
+        b_, a_, u_ = stage_model(k, Q, V, M, E, w.res, act)
+        st = {"ms": round(ms, 4)}
+        if b_ == "hbm" and a_:
+            st["GB/s"] = round(a_ / (ms / 1e3) / 1e9, 1)
+            st["frac_hbm"] = round(a_ / (ms / 1e3) / 1e9 / hbm_peak, 3)
+        stages[k] = st
+
+    # end to end through the C-ABI with host buffers: pinned target in, vertices + stats out
+    tgt_host = torch.from_numpy(w.target.copy()).pin_memory()
+    verts_host = torch.empty((V, 3), dtype=torch.float32).pin_memory()
+    B.pdg_fit_frame(ctx, tgt_host, 5)  # warm: same path, short frame
+    B.pdg_get_vertices(ctx, verts_host)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    stats = B.pdg_fit_frame(ctx, tgt_host, STEPS_PER_FRAME_E2E)
+    B.pdg_get_vertices(ctx, verts_host)
+    t_e2e = time.perf_counter() - t0
+    barrier()
+    if dist is not None:
+        tt = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    e2e = {"value": world * STEPS_PER_FRAME_E2E / t_e2e, "unit": "steps/s",
+           "h2d_bytes_per_step": M * 12 / STEPS_PER_FRAME_E2E,
+           "d2h_bytes_per_step": (V * 12 + 48) / STEPS_PER_FRAME_E2E,
+           "frame": f"pdg_fit_frame({STEPS_PER_FRAME_E2E} steps, host target) + pdg_get_vertices(host)",
+           "final_loss": stats.loss_total}
+    B.pdg_destroy(ctx)
+
+    launches_per_step = 17
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import pdg_oracle as O
+
+        cfgo = O.Config(res=w.res)
+        st = O.begin_frame(w.template, w.source, w.target, w.edges, cfgo)
+        t0 = time.perf_counter()
+        O.step(st, cfgo)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 1.0 / dt, "unit": "steps/s", "cores": 1, "kind": "oracle",
+               "sample": "1 full FP64 oracle step of the headline workload (numpy, single thread)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}" if world > 1 else "single",
+                       "l2": "flushed between steps (256 MiB write)", "grids": list(w.res),
+                       "V": V, "N": N, "M": M, "E": E},
+            "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+            "roofline": roof, "cpu_baseline": cpu, "stages": stages,
+            "resident_l2_steps_per_s": 1000.0 / resident_ms, "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

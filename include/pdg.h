@@ -1,0 +1,183 @@
+/*
+ * pdg.h - C ABI of the GB300 (sm_103a) per-iteration step of
+ *         Preconditioned Deformation Grids (arXiv 2509.18097).
+ *
+ * The library fits, frame by frame, a multi-resolution displacement grid G_t that maps
+ * the previous frame's template vertices X_{t-1} and source points P_{t-1} onto the
+ * target cloud P_t (Sec. 3, problem statement).  One optimisation iteration (a "step")
+ * is:
+ *   (a) y = x + (1/L) sum_l trilerp(G^l, x) on Q = X_{t-1} u P_{t-1}       (Sec. 3.1, Eq. 1)
+ *   (b) exact bidirectional robust-Chamfer nearest neighbours + gradient    (Sec. 3.4)
+ *   (c) weak edge isometry + gradient                                      (Sec. 3.4)
+ *   (d) adjoint of (a): point gradients into grid-vertex gradients         (chain rule of Eq. 1)
+ *   (e) (I + lambda_l L_l)^{-2} per level, then Adam with lr_l             (Sec. 3.2 Eq. 3, Sec. 3.6)
+ * Every stage runs in hand-written CUDA kernels; a step is replayed as one CUDA graph.
+ *
+ * Conventions (all entry points):
+ *  - Errors: nothing aborts.  Every call returns a pdg_status; pdg_last_error() gives
+ *    the message of the last failing call on a context.  A non-OK return leaves the
+ *    context usable, except PDG_ERR_CUDA caused by a sticky device error.
+ *  - Streams: `cuda_stream` is a cudaStream_t (NULL = the legacy default stream).  All
+ *    work is ordered on it; calls return without synchronising unless stated.
+ *  - Point arrays are float32 [n][3] (x, y, z interleaved, 12-byte stride).  Unless a
+ *    call says otherwise a pointer may be device memory (used in place, stream-ordered)
+ *    or host memory (pageable or pinned; copied in the call, which then synchronises
+ *    `cuda_stream` before returning so the caller may free it).
+ *  - Ownership: the library copies what it keeps (template, edges, current source
+ *    cloud, target); caller buffers need only live for the call.  Output buffers are
+ *    caller-allocated.
+ *  - Grid level l (0 = coarsest) has res[l] vertices per axis spanning [lo, hi] with
+ *    corners aligned; its values are float32 [res^3][3] indexed ((z*res + y)*res + x).
+ */
+#ifndef PDG_H
+#define PDG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PDG_MAX_LEVELS 8
+
+typedef enum pdg_status {
+  PDG_OK = 0,
+  PDG_ERR_INVALID = 1,   /* bad argument (sizes, NULL, non-finite input, config) */
+  PDG_ERR_OOM = 2,       /* device allocation failed */
+  PDG_ERR_BUDGET = 3,    /* request exceeds a memory budget or a fixed capacity */
+  PDG_ERR_CUDA = 4,      /* a CUDA runtime call failed */
+  PDG_ERR_NONFINITE = 5, /* a loss became NaN/Inf during a fit */
+  PDG_ERR_TIMEOUT = 6,   /* a bounded device-side wait gave up */
+  PDG_ERR_STATE = 7      /* call out of order (e.g. pdg_step outside a frame) */
+} pdg_status;
+
+/* Optimisation settings.  pdg_config_default() fills the paper's values:
+ * alpha = 5.56 (Sec. 3.4, w_R); w_iso = 250 (Sec. 3.4); Adam (0.9, 0.999, 1e-8),
+ * lr_l = 5e-3 * 1.1^l, lambda_l = 0.25 * 1.5^l with l = 0 the coarsest level (Sec. 3.6);
+ * without preconditioning the learning rate is scaled by 0.1 (Sec. 4, ablation). */
+typedef struct pdg_config {
+  int n_levels;               /* 1..PDG_MAX_LEVELS */
+  int res[PDG_MAX_LEVELS];    /* vertices per axis, coarse -> fine: 1 or a power of two <= 256 */
+  float lo[3], hi[3];         /* grid domain (default [-1.5, 1.5]^3); points outside are clamped */
+  float alpha;                /* robust Chamfer weight exp(-alpha d^2) */
+  float w_chamfer_mesh;       /* weight of CD_R(X_hat_t, P_t) (the confidence weight; 1) */
+  float w_chamfer_pts;        /* weight of CD_R(P_hat_t, P_t) (1) */
+  float w_iso;                /* isometry weight (250) */
+  float lr0, lr_growth;       /* per-level learning rate lr0 * lr_growth^l */
+  float lambda0, lambda_growth; /* per-level smoothness weight */
+  float beta1, beta2, eps;    /* Adam */
+  int precondition;           /* 1: (I + lambda L)^{-2} (Eq. 3); 0: raw gradient, lr x 0.1 */
+  int robust_weight_stopgrad; /* 1: the robust weight is not differentiated */
+  int warm_start;             /* 1: a frame starts from the previous frame's grids */
+} pdg_config;
+
+/* Losses of the last iteration of a frame (evaluated before that iteration's update). */
+typedef struct pdg_fit_stats {
+  double loss_total; /* w_mesh * cd_mesh + w_pts * cd_pts + w_iso * iso */
+  double cd_mesh;    /* CD_R(X_hat_t, P_t) */
+  double cd_pts;     /* CD_R(P_hat_t, P_t) */
+  double iso;        /* L_iso (unweighted) */
+  int n_steps;       /* iterations run in the frame */
+  int status;        /* pdg_status of the frame */
+} pdg_fit_stats;
+
+typedef struct pdg_ctx pdg_ctx;
+typedef struct pdg_batch pdg_batch;
+
+/* Fills `cfg` with the paper's defaults and levels 16, 32, 64, 128 over [-1.5, 1.5]^3. */
+void pdg_config_default(pdg_config* cfg);
+
+/* Device bytes a context with these sizes allocates (max_pts bounds every source and
+ * target cloud it will see).  0 on an invalid configuration. */
+size_t pdg_query_bytes(const pdg_config* cfg, int n_verts, int n_edges, int max_pts);
+
+/* Creates a fitting context for one sequence (Sec. 3, problem statement): the template
+ * mesh X_0 (verts [n_verts][3], edges int32 [n_edges][2], 0-based vertex ids) and the
+ * first source cloud P_0 ([n_src][3]).  max_pts (>= n_src) bounds all later clouds.
+ * Allocates all device memory up front.  Errors: PDG_ERR_INVALID (sizes, edge ids out of
+ * range, non-finite coordinates, config), PDG_ERR_OOM, PDG_ERR_CUDA. */
+pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_verts, const int32_t* edges,
+                      int n_edges, const float* source_xyz, int n_src, int max_pts, void* cuda_stream,
+                      pdg_ctx** out);
+
+/* Starts fitting G_t toward the target P_t ([n_tgt][3], 1 <= n_tgt <= max_pts): per-frame
+ * set-up (target cell grid, per-level point-to-vertex interpolation lists, edge rest
+ * lengths from X_{t-1}, grid/Adam reset).  PDG_ERR_STATE if a frame is already open. */
+pdg_status pdg_begin_frame(pdg_ctx* ctx, const float* target_xyz, int n_tgt, void* cuda_stream);
+
+/* Runs n_steps optimisation iterations of the open frame (one CUDA-graph replay each). */
+pdg_status pdg_step(pdg_ctx* ctx, int n_steps, void* cuda_stream);
+
+/* Closes the frame: X_t = X_{t-1} + u_t(X_{t-1}) with the final grids (Sec. 3.3) and
+ * P_t becomes the next source.  Synchronises `cuda_stream`; fills `stats` (may be NULL).
+ * Returns PDG_ERR_NONFINITE (frame still closed and advanced) if a loss was NaN/Inf. */
+pdg_status pdg_end_frame(pdg_ctx* ctx, pdg_fit_stats* stats, void* cuda_stream);
+
+/* pdg_begin_frame + pdg_step(n_steps) + pdg_end_frame. */
+pdg_status pdg_fit_frame(pdg_ctx* ctx, const float* target_xyz, int n_tgt, int n_steps, pdg_fit_stats* stats,
+                         void* cuda_stream);
+
+/* out = xyz + u(xyz) with the context's current grids (Eq. 1 / Sec. 3.3) for n arbitrary
+ * points; out_xyz is [n][3] in the same memory kind rules as inputs (host outputs are
+ * written before the call returns). */
+pdg_status pdg_deform(pdg_ctx* ctx, const float* xyz, int n, float* out_xyz, void* cuda_stream);
+
+/* Copies the current deformed template X_t ([n_verts][3]) to out_xyz (host or device). */
+pdg_status pdg_get_vertices(pdg_ctx* ctx, float* out_xyz, void* cuda_stream);
+
+/* Inspection of internal buffers (tests, autograd, debugging); out may be host or device.
+ * `level` is used by the per-level buffers.  out_bytes must be at least the size given. */
+enum pdg_buffer {
+  PDG_BUF_THETA = 0,    /* level values, float [res^3][3] */
+  PDG_BUF_GRAD = 1,     /* dLoss/dTheta of the last step, float [res^3][3] */
+  PDG_BUF_PGRAD = 2,    /* preconditioned gradient of the last step, float [res^3][3]
+                           (only kept when pdg_set_debug(ctx, 1) was called) */
+  PDG_BUF_Y = 3,        /* deformed query points y of the last step, float [n_verts+n_src][3] */
+  PDG_BUF_POINT_GRAD = 4, /* dLoss/dy of the last step, float [n_verts+n_src][3] */
+  PDG_BUF_NN_FWD = 5,   /* int32 [n_verts+n_src]: nearest target point of each query */
+  PDG_BUF_NN_REV = 6,   /* int32 [2][n_tgt]: nearest template vertex / source point of each target point */
+  PDG_BUF_LOSS = 7,     /* double [4]: total, cd_mesh, cd_pts, iso of the last step */
+  PDG_BUF_SOURCE = 8    /* current source cloud P_{t-1}, float [n_src][3] */
+};
+pdg_status pdg_read(pdg_ctx* ctx, int which, int level, void* out, size_t out_bytes, void* cuda_stream);
+
+/* Overwrites level `level`'s values with theta (float [res^3][3], host or device) and
+ * resets its Adam moments.  Valid inside a frame (used to start from given grids). */
+pdg_status pdg_write_theta(pdg_ctx* ctx, int level, const float* theta, void* cuda_stream);
+
+/* Profiling: runs n_steps iterations of the open frame as eager launches of the same
+ * stages the step graph holds, bracketing each stage with CUDA events on `cuda_stream`,
+ * and writes the summed milliseconds per stage to stage_ms[pdg_profile_stages()].
+ * Synchronises the stream after every iteration.  The stages are listed by
+ * pdg_profile_stage_name(i). */
+int pdg_profile_stages(void);
+const char* pdg_profile_stage_name(int i);
+pdg_status pdg_profile_step(pdg_ctx* ctx, int n_steps, double* stage_ms, void* cuda_stream);
+
+/* 1: keep the preconditioned gradient of each step readable as PDG_BUF_PGRAD. */
+pdg_status pdg_set_debug(pdg_ctx* ctx, int keep_pgrad);
+
+void pdg_destroy(pdg_ctx* ctx);
+const char* pdg_status_string(pdg_status s);
+const char* pdg_last_error(const pdg_ctx* ctx);
+
+/* ---- batching (continuous batching of independent sequences) --------------------------
+ * A batch runs one iteration of every member context in one CUDA-graph launch of
+ * batched kernels (each kernel iterates over (job, work item) pairs of all members).
+ * Members must be inside a frame (pdg_begin_frame).  Membership may change between
+ * calls; results per context are the same as running it alone. */
+pdg_status pdg_batch_create(int max_jobs, pdg_batch** out);
+pdg_status pdg_batch_set(pdg_batch* b, pdg_ctx* const* ctxs, int n_jobs);
+pdg_status pdg_batch_step(pdg_batch* b, int n_steps, void* cuda_stream);
+void pdg_batch_destroy(pdg_batch* b);
+
+/* ---- checkpoint / resume (between frames) ------------------------------------------- */
+size_t pdg_state_bytes(const pdg_ctx* ctx);
+pdg_status pdg_save_state(pdg_ctx* ctx, void* host_buf, size_t n, void* cuda_stream);
+pdg_status pdg_load_state(pdg_ctx* ctx, const void* host_buf, size_t n, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PDG_H */

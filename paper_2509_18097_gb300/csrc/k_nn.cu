@@ -1,0 +1,264 @@
+// Exact nearest neighbours for the bidirectional robust Chamfer distance (Sec. 3.4) and
+// its gradient.  Four searches per step: template vertices and source points (the moving
+// sets) against the target cloud, and the target cloud against each moving set.
+//
+// The target (per frame) and the moving sets (per step) are counting-sorted into uniform
+// cell grids (see CellGrid).  A first kernel searches every query's 3x3x3 cell box with
+// one thread per query, queries taken in cell order so neighbouring lanes read the same
+// cells.  The answer is certified when the best squared distance is below the squared
+// distance from the query to the box's open faces (with a margin covering the rounding of
+// the cell assignment); otherwise the query is appended to a per-job list that a second,
+// warp-cooperative kernel searches ring by ring (lanes split the rows of each shell, a
+// __shfl min-reduction over (d^2, index) packed in 64 bits picks the lexicographic minimum,
+// i.e. the lowest index on ties), falling back to an exhaustive scan of the set beyond
+// NN_RMAX rings.  Both kernels compare candidates with the same fp32 expression, so the
+// result is the exact lexicographic minimum of (fp32 d^2, index) over the whole set.
+#include <float.h>
+
+#include "kernels.h"
+
+namespace pdg {
+
+struct Best {
+  float d2;
+  int idx;
+  float x, y, z;
+};
+
+__device__ __forceinline__ void consider(Best& b, const float4 p, float qx, float qy, float qz) {
+  const float d2 = sqdist(qx, qy, qz, p.x, p.y, p.z);
+  const int id = __float_as_int(p.w);
+  if (d2 < b.d2 || (d2 == b.d2 && id < b.idx)) {
+    b.d2 = d2;
+    b.idx = id;
+    b.x = p.x;
+    b.y = p.y;
+    b.z = p.z;
+  }
+}
+
+// Squared lower bound on the distance from q to any point assigned to a cell outside the
+// box [c - r, c + r] (per axis, clipped to the grid).  FLT_MAX if the box covers the grid.
+__device__ __forceinline__ float outside_bound2(const CellGrid& g, float qx, float qy, float qz, int cx, int cy,
+                                                int cz, int r) {
+  const int G = 1 << g.bits;
+  const float q[3] = {qx, qy, qz};
+  const int c[3] = {cx, cy, cz};
+  float d = FLT_MAX;
+  float hmin = FLT_MAX;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    hmin = fminf(hmin, g.h[a]);
+    if (c[a] - r > 0) d = fminf(d, q[a] - (g.lo[a] + (float)(c[a] - r) * g.h[a]));
+    if (c[a] + r < G - 1) d = fminf(d, (g.lo[a] + (float)(c[a] + r + 1) * g.h[a]) - q[a]);
+  }
+  if (d == FLT_MAX) return FLT_MAX;
+  d -= 1e-4f * hmin;  // cell assignment and face positions are rounded in fp32
+  if (d <= 0.f) return 0.f;
+  return d * d * (1.f - 4e-6f);
+}
+
+// ------------------------------------------------------------------------------ finalise
+
+// forward query: moving point a (Q index qid) -> nearest target point b
+__device__ __forceinline__ void finalize_fwd(const Job& J, int qid, float ax, float ay, float az, const Best& b) {
+  const float s = b.d2;
+  const float e = expf(-J.alpha * s);
+  const float phi = s * e;
+  const float dphi = J.stopgrad ? e : e * (1.f - J.alpha * s);
+  const bool mesh = qid < J.V;
+  const float coef = 2.f * dphi * (mesh ? J.w_mesh / (float)J.V : J.w_pts / (float)(J.Q - J.V));
+  J.loss_fwd[qid] = phi;
+  J.gfwd[qid] = make_float4(coef * (ax - b.x), coef * (ay - b.y), coef * (az - b.z), 0.f);
+  J.nn_fwd[qid] = b.idx;
+}
+
+// reverse query: target point bq (index bid) -> nearest moving point a of set `set`
+__device__ __forceinline__ void finalize_rev(const Job& J, int set, int bid, float bx, float by, float bz,
+                                             const Best& a) {
+  const float s = a.d2;
+  const float e = expf(-J.alpha * s);
+  const float phi = s * e;
+  const float dphi = J.stopgrad ? e : e * (1.f - J.alpha * s);
+  J.loss_rev[set * J.M + bid] = phi;
+  J.nn_rev[set * J.M + bid] = a.idx - (set ? J.V : 0);
+  const float c = 2.f * dphi;
+  unsigned long long* acc = reinterpret_cast<unsigned long long*>(J.acc + 3 * (size_t)a.idx);
+  atomicAdd(acc + 0, (unsigned long long)to_fx(c * (a.x - bx)));
+  atomicAdd(acc + 1, (unsigned long long)to_fx(c * (a.y - by)));
+  atomicAdd(acc + 2, (unsigned long long)to_fx(c * (a.z - bz)));
+}
+
+// Resolves a query item of a job into its point, grid and set.
+// items [0, Q): forward queries in moving-grid order; [Q, Q + 2M): reverse queries
+// (set 0 then set 1) in target-grid order.
+struct QueryRef {
+  float x, y, z;
+  int id;    // Q index (forward) or target index (reverse)
+  int set;   // grid set searched
+  bool fwd;
+};
+
+__device__ __forceinline__ QueryRef resolve(const Job& J, int item) {
+  QueryRef q;
+  float4 p;
+  if (item < J.Q) {
+    p = J.mov.pts[item];
+    q.fwd = true;
+    q.set = 0;
+  } else {
+    const int r = item - J.Q;
+    q.set = r >= J.M ? 1 : 0;
+    p = J.tgt.pts[r - q.set * J.M];
+    q.fwd = false;
+  }
+  q.x = p.x; q.y = p.y; q.z = p.z;
+  q.id = __float_as_int(p.w);
+  return q;
+}
+
+__device__ __forceinline__ void finalize(const Job& J, const QueryRef& q, const Best& b) {
+  if (b.idx == 0x7fffffff || !(b.d2 < FLT_MAX)) {  // nothing found (non-finite coordinates)
+    if (q.fwd) {
+      J.loss_fwd[q.id] = __int_as_float(0x7fc00000);
+      J.gfwd[q.id] = make_float4(0.f, 0.f, 0.f, 0.f);
+      J.nn_fwd[q.id] = -1;
+    } else {
+      J.loss_rev[q.set * J.M + q.id] = __int_as_float(0x7fc00000);
+      J.nn_rev[q.set * J.M + q.id] = -1;
+    }
+    return;
+  }
+  if (q.fwd) finalize_fwd(J, q.id, q.x, q.y, q.z, b);
+  else finalize_rev(J, q.set, q.id, q.x, q.y, q.z, b);
+}
+
+// ------------------------------------------------------------------------------ one-ring pass
+
+__global__ void __launch_bounds__(256) k_nn(const Plan* __restrict__ P) {
+  const int nj = P->n_jobs;
+  const int total = P->pre[ST_NNQ][nj];
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+    const int j = find_job(P->pre[ST_NNQ], nj, it);
+    const Job& J = *P->jobs[j];
+    const int item = it - P->pre[ST_NNQ][j];
+    const QueryRef q = resolve(J, item);
+    const CellGrid& g = q.fwd ? J.tgt : J.mov;
+    const int G = 1 << g.bits;
+    const int base = q.set * G * G * G;
+    const int cx = cell_coord(q.x, g.lo[0], g.inv_h[0], G);
+    const int cy = cell_coord(q.y, g.lo[1], g.inv_h[1], G);
+    const int cz = cell_coord(q.z, g.lo[2], g.inv_h[2], G);
+    const int x0 = max(cx - 1, 0), x1 = min(cx + 1, G - 1);
+    Best b{FLT_MAX, 0x7fffffff, 0.f, 0.f, 0.f};
+    for (int zz = max(cz - 1, 0); zz <= min(cz + 1, G - 1); ++zz) {
+      for (int yy = max(cy - 1, 0); yy <= min(cy + 1, G - 1); ++yy) {
+        const int rk = base + row_key(yy, zz, g.bits);
+        const int s = __ldg(g.off + rk + x0), e = __ldg(g.off + rk + x1 + 1);
+        for (int k = s; k < e; ++k) consider(b, __ldg(g.pts + k), q.x, q.y, q.z);
+      }
+    }
+    if (b.d2 < outside_bound2(g, q.x, q.y, q.z, cx, cy, cz, 1)) {
+      finalize(J, q, b);
+    } else {
+      const int slot = atomicAdd(J.hard_count, 1);
+      J.hard[slot] = item;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------ ring pass
+
+__device__ __forceinline__ unsigned long long pack(const Best& b) {
+  return ((unsigned long long)__float_as_uint(b.d2) << 32) | (unsigned)b.idx;
+}
+
+// lexicographic (d2, idx) minimum over the warp; every lane receives it
+__device__ __forceinline__ Best warp_min(const Best& b) {
+  unsigned long long m = pack(b);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+    m = t < m ? t : m;
+  }
+  const unsigned ball = __ballot_sync(0xffffffffu, pack(b) == m);
+  const int src = __ffs(ball) - 1;
+  Best r;
+  r.d2 = __uint_as_float((unsigned)(m >> 32));
+  r.idx = (int)(unsigned)(m & 0xffffffffu);
+  r.x = __shfl_sync(0xffffffffu, b.x, src);
+  r.y = __shfl_sync(0xffffffffu, b.y, src);
+  r.z = __shfl_sync(0xffffffffu, b.z, src);
+  return r;
+}
+
+__device__ __forceinline__ void scan_range(const CellGrid& g, int s, int e, const QueryRef& q, Best& b) {
+  for (int k = s; k < e; ++k) consider(b, __ldg(g.pts + k), q.x, q.y, q.z);
+}
+
+__global__ void __launch_bounds__(256) k_nn_hard(const Plan* __restrict__ P) {
+  __shared__ int hpre[MAXJ + 1];
+  const int nj = P->n_jobs;
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int j = 0; j < nj; ++j) {
+      hpre[j] = acc;
+      acc += *P->jobs[j]->hard_count;
+    }
+    hpre[nj] = acc;
+  }
+  __syncthreads();
+  const int total = hpre[nj];
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nwarps) {
+    int lo = 0, hi = nj;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (hpre[mid] <= w) lo = mid; else hi = mid;
+    }
+    const Job& J = *P->jobs[lo];
+    const int item = J.hard[w - hpre[lo]];
+    const QueryRef q = resolve(J, item);
+    const CellGrid& g = q.fwd ? J.tgt : J.mov;
+    const int G = 1 << g.bits;
+    const int base = q.set * G * G * G;
+    const int cx = cell_coord(q.x, g.lo[0], g.inv_h[0], G);
+    const int cy = cell_coord(q.y, g.lo[1], g.inv_h[1], G);
+    const int cz = cell_coord(q.z, g.lo[2], g.inv_h[2], G);
+    Best b{FLT_MAX, 0x7fffffff, 0.f, 0.f, 0.f};
+    Best best = b;
+    bool done = false;
+    for (int r = 0; r <= NN_RMAX && !done; ++r) {
+      // shell r: rows (dy, dz) in [-r, r]^2; rows on the shell's y/z boundary are scanned
+      // over the full x range, the others only at x = c -/+ r
+      const int side = 2 * r + 1;
+      for (int ri = lane; ri < side * side; ri += 32) {
+        const int dy = ri % side - r, dz = ri / side - r;
+        const int yy = cy + dy, zz = cz + dz;
+        if (yy < 0 || yy >= G || zz < 0 || zz >= G) continue;
+        const int rk = base + row_key(yy, zz, g.bits);
+        if (max(abs(dy), abs(dz)) == r) {
+          const int x0 = max(cx - r, 0), x1 = min(cx + r, G - 1);
+          scan_range(g, __ldg(g.off + rk + x0), __ldg(g.off + rk + x1 + 1), q, b);
+        } else {
+          if (cx - r >= 0) scan_range(g, __ldg(g.off + rk + cx - r), __ldg(g.off + rk + cx - r + 1), q, b);
+          if (cx + r < G) scan_range(g, __ldg(g.off + rk + cx + r), __ldg(g.off + rk + cx + r + 1), q, b);
+        }
+      }
+      best = warp_min(b);
+      done = best.d2 < outside_bound2(g, q.x, q.y, q.z, cx, cy, cz, r);
+    }
+    if (!done) {  // exhaustive scan of the set
+      const int s = __ldg(g.off + base), e = __ldg(g.off + base + G * G * G);
+      for (int k = s + lane; k < e; k += 32) consider(b, __ldg(g.pts + k), q.x, q.y, q.z);
+      best = warp_min(b);
+    }
+    if (lane == 0) finalize(J, q, best);
+  }
+}
+
+void launch_nn(const Plan* P, int grid, cudaStream_t s) { k_nn<<<grid, 256, 0, s>>>(P); }
+void launch_nn_hard(const Plan* P, int grid, cudaStream_t s) { k_nn_hard<<<grid, 256, 0, s>>>(P); }
+
+}  // namespace pdg

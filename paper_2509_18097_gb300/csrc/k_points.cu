@@ -1,0 +1,356 @@
+// Point- and edge-parallel kernels of the step: the plan, multi-level trilinear
+// evaluation (Eq. 1), the moving-set cell keys, edge isometry (Sec. 3.4), gradient
+// assembly and the loss reduction; plus the per-frame set-up kernels.
+#include "kernels.h"
+
+namespace pdg {
+
+// ------------------------------------------------------------------------------ plan
+
+// Computes, on the device, the per-stage item prefixes over the jobs of a plan and (when
+// `bump`) advances each job's Adam step count and its bias-correction factors.  One block.
+__global__ void k_plan(Plan* P, int bump) {
+  __shared__ int cnt[NSTAGE][MAXJ];
+  const int nj = P->n_jobs;
+  for (int j = threadIdx.x; j < nj; j += blockDim.x) {
+    Job* J = P->jobs[j];
+    if (bump) {
+      int k = *J->step + 1;
+      *J->step = k;
+      *J->hard_count = 0;
+      J->bias[0] = (float)(1.0 / (1.0 - pow((double)J->beta1, (double)k)));
+      J->bias[1] = (float)(1.0 / sqrt(1.0 - pow((double)J->beta2, (double)k)));
+    }
+    const int G = 1 << J->mov.bits;
+    cnt[ST_Q][j] = J->Q;
+    cnt[ST_NNQ][j] = J->Q + 2 * J->M;
+    cnt[ST_E][j] = J->E;
+    cnt[ST_MOVCH][j] = (2 * G * G * G + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    int a = 0, t = 0;
+    for (int l = 0; l < J->L; ++l) {
+      a += *J->lev[l].n_active;
+      t += J->lev[l].tiles;
+    }
+    cnt[ST_ADJ][j] = a;
+    cnt[ST_TILE][j] = t;
+    cnt[ST_JOB][j] = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x < NSTAGE) {
+    const int s = threadIdx.x;
+    int acc = 0;
+    P->pre[s][0] = 0;
+    for (int j = 0; j < nj; ++j) {
+      acc += cnt[s][j];
+      P->pre[s][j + 1] = acc;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------ (a) eval
+
+// u(p) = (1/L) sum_l sum_{8 corners} w * theta_l[corner]   (Eq. 1; vertex-aligned levels,
+// coordinates clamped to the domain, last cell closed)
+__device__ float3 eval_disp(const Job& J, float px, float py, float pz) {
+  float ux = 0.f, uy = 0.f, uz = 0.f;
+  for (int l = 0; l < J.L; ++l) {
+    const Level& lv = J.lev[l];
+    const int n = lv.n;
+    if (n == 1) {
+      const float4 t = lv.theta[0];
+      ux += t.x; uy += t.y; uz += t.z;
+      continue;
+    }
+    const float nm1 = (float)(n - 1);
+    float tx = (px - J.lo[0]) * (nm1 / (J.hi[0] - J.lo[0]));
+    float ty = (py - J.lo[1]) * (nm1 / (J.hi[1] - J.lo[1]));
+    float tz = (pz - J.lo[2]) * (nm1 / (J.hi[2] - J.lo[2]));
+    tx = fminf(fmaxf(tx, 0.f), nm1);
+    ty = fminf(fmaxf(ty, 0.f), nm1);
+    tz = fminf(fmaxf(tz, 0.f), nm1);
+    const int ix = min((int)floorf(tx), n - 2), iy = min((int)floorf(ty), n - 2), iz = min((int)floorf(tz), n - 2);
+    const float fx = tx - ix, fy = ty - iy, fz = tz - iz;
+    const float4* t0 = lv.theta + ((size_t)(iz * n + iy) * n + ix);
+    const float4* t1 = t0 + (size_t)n * n;
+    const float4 c000 = t0[0], c100 = t0[1], c010 = t0[n], c110 = t0[n + 1];
+    const float4 c001 = t1[0], c101 = t1[1], c011 = t1[n], c111 = t1[n + 1];
+    const float gx = 1.f - fx, gy = 1.f - fy, gz = 1.f - fz;
+    const float w000 = gx * gy * gz, w100 = fx * gy * gz, w010 = gx * fy * gz, w110 = fx * fy * gz;
+    const float w001 = gx * gy * fz, w101 = fx * gy * fz, w011 = gx * fy * fz, w111 = fx * fy * fz;
+    ux += w000 * c000.x + w100 * c100.x + w010 * c010.x + w110 * c110.x + w001 * c001.x + w101 * c101.x +
+          w011 * c011.x + w111 * c111.x;
+    uy += w000 * c000.y + w100 * c100.y + w010 * c010.y + w110 * c110.y + w001 * c001.y + w101 * c101.y +
+          w011 * c011.y + w111 * c111.y;
+    uz += w000 * c000.z + w100 * c100.z + w010 * c010.z + w110 * c110.z + w001 * c001.z + w101 * c101.z +
+          w011 * c011.z + w111 * c111.z;
+  }
+  const float invL = 1.f / (float)J.L;
+  return make_float3(ux * invL, uy * invL, uz * invL);
+}
+
+// y = x + u(x) on Q; the cell key of y in the moving grid (set 0: template, set 1: source)
+// and its count; clears the point's fixed-point reverse-Chamfer accumulator.
+__global__ void k_interp(const Plan* __restrict__ P) {
+  const int nj = P->n_jobs;
+  const int total = P->pre[ST_Q][nj];
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+    const int j = find_job(P->pre[ST_Q], nj, it);
+    const Job& J = *P->jobs[j];
+    const int p = it - P->pre[ST_Q][j];
+    const float4 x = J.x[p];
+    const float3 u = eval_disp(J, x.x, x.y, x.z);
+    const float4 y = make_float4(x.x + u.x, x.y + u.y, x.z + u.z, 0.f);
+    J.y[p] = y;
+    const int key = cell_key(J.mov, y.x, y.y, y.z, p < J.V ? 0 : 1);
+    J.mov.keys[p] = key;
+    atomicAdd(&J.mov.hist[key], 1);
+    J.acc[3 * p + 0] = 0;
+    J.acc[3 * p + 1] = 0;
+    J.acc[3 * p + 2] = 0;
+  }
+}
+
+// scatter of the moving points into key order (counts return to zero)
+__global__ void k_mov_scatter(const Plan* __restrict__ P) {
+  const int nj = P->n_jobs;
+  const int total = P->pre[ST_Q][nj];
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+    const int j = find_job(P->pre[ST_Q], nj, it);
+    const Job& J = *P->jobs[j];
+    const int p = it - P->pre[ST_Q][j];
+    const int key = J.mov.keys[p];
+    const int pos = J.mov.off[key] + atomicSub(&J.mov.hist[key], 1) - 1;
+    const float4 y = J.y[p];
+    J.mov.pts[pos] = make_float4(y.x, y.y, y.z, __int_as_float(p));
+  }
+}
+
+// ------------------------------------------------------------------------------ (c) isometry
+
+// |a - b| with explicit rounding so every kernel computes it bit-identically
+__device__ __forceinline__ float edge_len(float4 a, float4 b) {
+  return __fsqrt_rn(sqdist(a.x, a.y, a.z, b.x, b.y, b.z));
+}
+
+// per edge: |r| with r = |y_i - y_j| - e_prev, and sgn(r)(y_i - y_j)/(|y_i - y_j| |E|)
+// (Sec. 3.4; sgn(0) = 0, zero-length edges contribute no gradient)
+__global__ void k_iso_edges(const Plan* __restrict__ P) {
+  const int nj = P->n_jobs;
+  const int total = P->pre[ST_E][nj];
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+    const int j = find_job(P->pre[ST_E], nj, it);
+    const Job& J = *P->jobs[j];
+    const int e = it - P->pre[ST_E][j];
+    const int2 ij = J.edges[e];
+    const float4 a = J.y[ij.x], b = J.y[ij.y];
+    const float len = edge_len(a, b);
+    const float r = len - J.e_prev[e];
+    J.loss_iso[e] = fabsf(r);
+    float c = 0.f;
+    if (len > 0.f && r != 0.f) c = copysignf(1.f, r) / (len * (float)J.E);
+    J.edge_d[e] = make_float4(c * (a.x - b.x), c * (a.y - b.y), c * (a.z - b.z), 0.f);
+  }
+}
+
+// dLoss/dy = forward Chamfer term + (w/M) * reverse Chamfer sums + w_iso * isometry
+// gradient gathered over the vertex's edges in a fixed order.
+__global__ void k_assemble(const Plan* __restrict__ P) {
+  const int nj = P->n_jobs;
+  const int total = P->pre[ST_Q][nj];
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+    const int j = find_job(P->pre[ST_Q], nj, it);
+    const Job& J = *P->jobs[j];
+    const int p = it - P->pre[ST_Q][j];
+    float4 g = J.gfwd[p];
+    const float wr = (p < J.V ? J.w_mesh : J.w_pts) / (float)J.M;
+    g.x += wr * from_fx(J.acc[3 * p + 0]);
+    g.y += wr * from_fx(J.acc[3 * p + 1]);
+    g.z += wr * from_fx(J.acc[3 * p + 2]);
+    if (p < J.V && J.w_iso != 0.f) {
+      float ix = 0.f, iy = 0.f, iz = 0.f;
+      for (int k = J.v2e_ptr[p]; k < J.v2e_ptr[p + 1]; ++k) {
+        const int ent = J.v2e[k];
+        const float4 d = J.edge_d[ent >> 1];
+        if (ent & 1) { ix -= d.x; iy -= d.y; iz -= d.z; }
+        else { ix += d.x; iy += d.y; iz += d.z; }
+      }
+      g.x += J.w_iso * ix;
+      g.y += J.w_iso * iy;
+      g.z += J.w_iso * iz;
+    }
+    J.gy[p] = g;
+  }
+}
+
+// ------------------------------------------------------------------------------ loss
+
+// Fixed-order FP64 reduction of the per-query and per-edge terms into the job's loss
+// record: cd_mesh = mean_X phi + mean_P_t phi, cd_pts likewise, iso = mean |r|.
+__global__ void k_loss(const Plan* __restrict__ P) {
+  __shared__ double red[5][32];
+  const int nj = P->n_jobs;
+  for (int j = blockIdx.x; j < nj; j += gridDim.x) {
+    const Job& J = *P->jobs[j];
+    double s[5] = {0, 0, 0, 0, 0};
+    for (int i = threadIdx.x; i < J.Q; i += blockDim.x) s[i < J.V ? 0 : 1] += (double)J.loss_fwd[i];
+    for (int i = threadIdx.x; i < J.M; i += blockDim.x) {
+      s[2] += (double)J.loss_rev[i];
+      s[3] += (double)J.loss_rev[J.M + i];
+    }
+    for (int i = threadIdx.x; i < J.E; i += blockDim.x) s[4] += (double)J.loss_iso[i];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      double v = s[k];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) red[k][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t[5];
+      for (int k = 0; k < 5; ++k) {
+        double v = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += red[k][q];
+        t[k] = v;
+      }
+      const double cdm = t[0] / J.V + t[2] / J.M;
+      const double cdp = t[1] / (J.Q - J.V) + t[3] / J.M;
+      const double iso = J.E > 0 ? t[4] / J.E : 0.0;
+      const double tot = (double)J.w_mesh * cdm + (double)J.w_pts * cdp + (double)J.w_iso * iso;
+      J.loss[0] = tot;
+      J.loss[1] = cdm;
+      J.loss[2] = cdp;
+      J.loss[3] = iso;
+      if (!isfinite(tot)) *J.status |= 1;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------ per frame
+
+__global__ void k_pack4(const float* __restrict__ in, float4* __restrict__ out, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = make_float4(in[3 * i], in[3 * i + 1], in[3 * i + 2], 0.f);
+}
+
+__global__ void k_unpack4(const float4* __restrict__ in, float* __restrict__ out, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float4 v = in[i];
+    out[3 * i] = v.x;
+    out[3 * i + 1] = v.y;
+    out[3 * i + 2] = v.z;
+  }
+}
+
+__global__ void k_check_finite(const float* __restrict__ in, int n, int* flag) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    if (!isfinite(in[i])) atomicOr(flag, 1);
+}
+
+// Q = X_{t-1} u P_{t-1}; rest lengths e_prev from X_{t-1} (same expression as k_iso_edges
+// so that zero grids give r == 0 exactly).
+__global__ void k_frame_points(Job* J) {
+  const int Q = J->Q, V = J->V;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < Q; p += gridDim.x * blockDim.x)
+    J->x[p] = p < V ? J->verts4[p] : J->src4[p - V];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < J->E; e += gridDim.x * blockDim.x) {
+    const int2 ij = J->edges[e];
+    J->e_prev[e] = edge_len(J->verts4[ij.x], J->verts4[ij.y]);
+  }
+}
+
+__global__ void k_tgt_keys(Job* J) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < J->M; p += gridDim.x * blockDim.x) {
+    const float4 t = J->tgt4[p];
+    const int key = cell_key(J->tgt, t.x, t.y, t.z, 0);
+    J->tgt.keys[p] = key;
+    atomicAdd(&J->tgt.hist[key], 1);
+  }
+}
+
+__global__ void k_tgt_scatter(Job* J) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < J->M; p += gridDim.x * blockDim.x) {
+    const int key = J->tgt.keys[p];
+    const int pos = J->tgt.off[key] + atomicSub(&J->tgt.hist[key], 1) - 1;
+    const float4 t = J->tgt4[p];
+    J->tgt.pts[pos] = make_float4(t.x, t.y, t.z, __int_as_float(p));
+  }
+}
+
+// frame end: X_t = X_{t-1} + u_t(X_{t-1}) with the final grids (Sec. 3.3)
+__global__ void k_end_frame(Job* J) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < J->V; p += gridDim.x * blockDim.x) {
+    const float4 x = J->x[p];
+    const float3 u = eval_disp(*J, x.x, x.y, x.z);
+    J->verts4[p] = make_float4(x.x + u.x, x.y + u.y, x.z + u.z, 0.f);
+  }
+}
+
+// out = xyz + u(xyz) for arbitrary points ([n][3] float in/out, device)
+__global__ void k_deform(const Job* __restrict__ J, const float* __restrict__ in, float* __restrict__ out, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float px = in[3 * i], py = in[3 * i + 1], pz = in[3 * i + 2];
+    const float3 u = eval_disp(*J, px, py, pz);
+    out[3 * i] = px + u.x;
+    out[3 * i + 1] = py + u.y;
+    out[3 * i + 2] = pz + u.z;
+  }
+}
+
+// ------------------------------------------------------------------------------ launchers
+
+static inline int blocks_for(int n, int threads) { return max(1, min((n + threads - 1) / threads, 4096)); }
+
+void launch_plan(Plan* P, int bump, cudaStream_t s) { k_plan<<<1, 256, 0, s>>>(P, bump); }
+void launch_interp(const Plan* P, int grid, cudaStream_t s) { k_interp<<<grid, 256, 0, s>>>(P); }
+void launch_mov_scatter(const Plan* P, int grid, cudaStream_t s) { k_mov_scatter<<<grid, 256, 0, s>>>(P); }
+void launch_iso_edges(const Plan* P, int grid, cudaStream_t s) { k_iso_edges<<<grid, 256, 0, s>>>(P); }
+void launch_assemble(const Plan* P, int grid, cudaStream_t s) { k_assemble<<<grid, 256, 0, s>>>(P); }
+void launch_loss(const Plan* P, int grid, cudaStream_t s) { k_loss<<<grid, 512, 0, s>>>(P); }
+
+void launch_pack4(const float* in, float4* out, int n, cudaStream_t s) {
+  k_pack4<<<blocks_for(n, 256), 256, 0, s>>>(in, out, n);
+}
+void launch_unpack4(const float4* in, float* out, int n, cudaStream_t s) {
+  k_unpack4<<<blocks_for(n, 256), 256, 0, s>>>(in, out, n);
+}
+void launch_check_finite(const float* in, int n, int* flag, cudaStream_t s) {
+  k_check_finite<<<blocks_for(n, 256), 256, 0, s>>>(in, n, flag);
+}
+void launch_frame_points(Job* J, int Q, int E, cudaStream_t s) {
+  k_frame_points<<<blocks_for(max(Q, E), 256), 256, 0, s>>>(J);
+}
+void launch_end_frame(Job* J, int V, cudaStream_t s) { k_end_frame<<<blocks_for(V, 256), 256, 0, s>>>(J); }
+void launch_deform(const Job* J, const float* in, float* out, int n, cudaStream_t s) {
+  k_deform<<<blocks_for(n, 256), 256, 0, s>>>(J, in, out, n);
+}
+
+__global__ void k_soa_to_aos(const float* __restrict__ in, float* __restrict__ out, int n3) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += gridDim.x * blockDim.x) {
+    out[3 * i] = in[i];
+    out[3 * i + 1] = in[n3 + i];
+    out[3 * i + 2] = in[2 * n3 + i];
+  }
+}
+__global__ void k_copy_int(const int* __restrict__ in, int* __restrict__ out, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = in[i];
+}
+void launch_soa_to_aos(const float* in, float* out, int n3, cudaStream_t s) {
+  k_soa_to_aos<<<blocks_for(n3, 256), 256, 0, s>>>(in, out, n3);
+}
+void launch_aos_to_float4(const float* in, float4* out, int n, cudaStream_t s) { launch_pack4(in, out, n, s); }
+void launch_copy_int(const int* in, int* out, int n, cudaStream_t s) {
+  k_copy_int<<<blocks_for(n, 256), 256, 0, s>>>(in, out, n);
+}
+
+// target cell grid of the frame: keys + counts, exclusive scan, scatter
+void launch_tgt_build(Job* J, const Job& hJ, cudaStream_t s) {
+  k_tgt_keys<<<blocks_for(hJ.M, 256), 256, 0, s>>>(J);
+  const int G = 1 << hJ.tgt.bits;
+  ScanSeg seg{hJ.tgt.hist, hJ.tgt.off, G * G * G, hJ.tgt.csum};
+  launch_scan_segments(&seg, 1, nullptr, nullptr, s);
+  k_tgt_scatter<<<blocks_for(hJ.M, 256), 256, 0, s>>>(J);
+}
+
+}  // namespace pdg

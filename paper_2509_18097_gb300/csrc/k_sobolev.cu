@@ -1,0 +1,229 @@
+// Grid Sobolev preconditioning (Sec. 3.2, Eq. 3) fused with the Adam update (Sec. 3.6).
+//
+// L_l is the 6-neighbour graph Laplacian of the level's vertex grid with a free
+// boundary; it is the Kronecker sum of three path-graph Laplacians whose eigenvectors are
+// the DCT-II basis vectors cos(pi k (i + 1/2) / n) with eigenvalues mu_k = 4 sin^2(pi k / 2n).
+// Hence (I + lambda L)^{-2} g = C^{-1} diag((1 + lambda (mu_kx + mu_ky + mu_kz))^{-2}) C g
+// with C the separable (unnormalised) 3-D DCT-II.  It is applied in five passes over the
+// level, each pass loading tiles of 32 lines x 3 channels into shared memory:
+//   1: x-lines of g, DCT-II                   -> tmp
+//   2: y-lines,      DCT-II                   -> tmp
+//   3: z-lines,      DCT-II, spectral scale (incl. 1/n^3), inverse -> tmp
+//   4: y-lines,      inverse
+//   5: x-lines,      inverse, then Adam on theta/m/v of those vertices.
+// A line transform of length n = 2^p is done two lines at a time by one warp: the lines
+// are packed as the real and imaginary parts of one complex sequence (after the
+// even/odd reordering that turns a DCT-II into a DFT), transformed by a radix-2 Stockham
+// FFT in shared memory, and separated with the conjugate-symmetry of real spectra.
+#include "kernels.h"
+
+namespace pdg {
+
+constexpr int TS = 33;  // padded tile stride (floats) between consecutive elements of a line
+
+int sobolev_smem_bytes(int n) { return 3 * n * TS * 4 + SOB_WARPS * 2 * n * 8; }
+
+template <bool INV>
+__device__ __forceinline__ float2* fft_warp(float2* src, float2* dst, const float2* __restrict__ tw, int n,
+                                            int lane) {
+  const int half = n >> 1;
+  for (int Ns = 1; Ns < n; Ns <<= 1) {
+    const int step = half / Ns;
+    for (int j = lane; j < half; j += 32) {
+      const int k = j & (Ns - 1);
+      float2 w = __ldg(tw + k * step);
+      if (INV) w.y = -w.y;
+      const float2 v0 = src[j], v1 = src[j + half];
+      const float2 t = make_float2(v1.x * w.x - v1.y * w.y, v1.x * w.y + v1.y * w.x);
+      const int d = ((j - k) << 1) + k;
+      dst[d] = make_float2(v0.x + t.x, v0.y + t.y);
+      dst[d + Ns] = make_float2(v0.x - t.x, v0.y - t.y);
+    }
+    __syncwarp();
+    float2* sw = src;
+    src = dst;
+    dst = sw;
+  }
+  return src;
+}
+
+__device__ __forceinline__ int dct_src(int j, int n) { return j < (n >> 1) ? 2 * j : 2 * (n - 1 - j) + 1; }
+
+// A, B <- C A, C B (unnormalised DCT-II), lines with element stride TS
+__device__ void dct2_pair(float* A, float* B, int n, float2* b0, float2* b1, const float2* __restrict__ tw,
+                          const float2* __restrict__ tw4, int lane) {
+  for (int j = lane; j < n; j += 32) {
+    const int s = dct_src(j, n) * TS;
+    b0[j] = make_float2(A[s], B[s]);
+  }
+  __syncwarp();
+  const float2* Z = fft_warp<false>(b0, b1, tw, n, lane);
+  for (int k = lane; k < n; k += 32) {
+    const float2 zk = Z[k];
+    const float2 zc = Z[(n - k) & (n - 1)];
+    // V_A = (Z_k + conj Z_{n-k}) / 2,  V_B = (Z_k - conj Z_{n-k}) / (2i)
+    const float2 va = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y - zc.y));
+    const float2 vb = make_float2(0.5f * (zk.y + zc.y), -0.5f * (zk.x - zc.x));
+    const float2 w = __ldg(tw4 + k);  // exp(-i pi k / 2n)
+    A[k * TS] = w.x * va.x - w.y * va.y;
+    B[k * TS] = w.x * vb.x - w.y * vb.y;
+  }
+  __syncwarp();
+}
+
+// A, B <- n C^{-1} A, n C^{-1} B (the 1/n is folded into the spectral scale)
+__device__ void dct3_pair(float* A, float* B, int n, float2* b0, float2* b1, const float2* __restrict__ tw,
+                          const float2* __restrict__ tw4, int lane) {
+  for (int k = lane; k < n; k += 32) {
+    const float a = A[k * TS], an = k ? A[(n - k) * TS] : 0.f;
+    const float b = B[k * TS], bn = k ? B[(n - k) * TS] : 0.f;
+    float2 w = __ldg(tw4 + k);
+    w.y = -w.y;  // exp(+i pi k / 2n)
+    // V = w (X_k - i X_{n-k});  Z = V_A + i V_B
+    const float2 va = make_float2(w.x * a + w.y * an, w.y * a - w.x * an);
+    const float2 vb = make_float2(w.x * b + w.y * bn, w.y * b - w.x * bn);
+    b0[k] = make_float2(va.x - vb.y, va.y + vb.x);
+  }
+  __syncwarp();
+  const float2* z = fft_warp<true>(b0, b1, tw, n, lane);
+  for (int j = lane; j < n; j += 32) {
+    const int s = dct_src(j, n) * TS;
+    A[s] = z[j].x;
+    B[s] = z[j].y;
+  }
+  __syncwarp();
+}
+
+// flat vertex index of element e of line r of a level (axis 0: x-lines, r = z n + y;
+// axis 1: y-lines, r = z n + x; axis 2: z-lines, r = y n + x)
+template <int AXIS>
+__device__ __forceinline__ int eaddr(int n, int lg, int r, int e) {
+  if (AXIS == 0) return (r << lg) + e;
+  const int lo = r & (n - 1), hi = r >> lg;
+  if (AXIS == 1) return (((hi << lg) + e) << lg) + lo;
+  return (((e << lg) + hi) << lg) + lo;
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(SOB_THREADS) k_sob(const Plan* __restrict__ P) {
+  constexpr int AXIS = (PASS == 1 || PASS == 5) ? 0 : (PASS == 2 || PASS == 4) ? 1 : 2;
+  extern __shared__ float smem[];
+  const int nj = P->n_jobs;
+  const int total = P->pre[ST_TILE][nj];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    const int j = find_job(P->pre[ST_TILE], nj, it);
+    const Job& J = *P->jobs[j];
+    const bool pre = J.precondition != 0;
+    if (PASS < 5 && !pre) continue;
+    int t = it - P->pre[ST_TILE][j];
+    int l = 0;
+    for (; l < J.L - 1; ++l) {
+      if (t < J.lev[l].tiles) break;
+      t -= J.lev[l].tiles;
+    }
+    const Level& lv = J.lev[l];
+    const int n = lv.n, lg = lv.lg, n3 = lv.n3, nl = n * n;
+    const int r0 = t * TILE_LINES;
+    float* tl = smem;
+    float2* b0 = reinterpret_cast<float2*>(smem + 3 * n * TS) + warp * 2 * n;
+    float2* b1 = b0 + n;
+    const float* src = (PASS == 1 || (PASS == 5 && !pre)) ? lv.g : lv.tmp;
+
+    for (int idx = threadIdx.x; idx < 3 * TILE_LINES * n; idx += SOB_THREADS) {
+      const int c = idx / (TILE_LINES * n);
+      const int rem = idx - c * TILE_LINES * n;
+      int tt, e;
+      if (AXIS == 0) { tt = rem >> lg; e = rem & (n - 1); }
+      else { e = rem >> 5; tt = rem & 31; }
+      const int r = r0 + tt;
+      tl[(c * n + e) * TS + tt] = r < nl ? src[(size_t)c * n3 + eaddr<AXIS>(n, lg, r, e)] : 0.f;
+    }
+    __syncthreads();
+
+    if (n > 1 && pre) {
+      for (int pp = warp; pp < 3 * TILE_LINES / 2; pp += SOB_WARPS) {
+        const int c = pp / (TILE_LINES / 2), tt = (pp % (TILE_LINES / 2)) * 2;
+        float* A = tl + c * n * TS + tt;
+        float* B = A + 1;
+        if (PASS == 1 || PASS == 2 || PASS == 3) dct2_pair(A, B, n, b0, b1, lv.tw, lv.tw4, lane);
+        if (PASS == 3) {
+          // spectral scale (1 + lambda (mu_kx + mu_ky + mu_kz))^{-2} / n^3; lines are
+          // z-lines r = ky n + kx
+          const int ra = r0 + tt, rb = ra + 1;
+          const float ma = __ldg(lv.mu + (ra & (n - 1))) + __ldg(lv.mu + ((ra >> lg) & (n - 1)));
+          const float mb = __ldg(lv.mu + (rb & (n - 1))) + __ldg(lv.mu + ((rb >> lg) & (n - 1)));
+          const float inv_n3 = 1.f / (float)n3;
+          for (int e = lane; e < n; e += 32) {
+            const float me = __ldg(lv.mu + e);
+            const float ia = 1.f / (1.f + lv.lam * (ma + me));
+            const float ib = 1.f / (1.f + lv.lam * (mb + me));
+            A[e * TS] *= ia * ia * inv_n3;
+            B[e * TS] *= ib * ib * inv_n3;
+          }
+          __syncwarp();
+        }
+        if (PASS >= 3) dct3_pair(A, B, n, b0, b1, lv.tw, lv.tw4, lane);
+      }
+    }
+    __syncthreads();
+
+    if (PASS < 5) {
+      for (int idx = threadIdx.x; idx < 3 * TILE_LINES * n; idx += SOB_THREADS) {
+        const int c = idx / (TILE_LINES * n);
+        const int rem = idx - c * TILE_LINES * n;
+        int tt, e;
+        if (AXIS == 0) { tt = rem >> lg; e = rem & (n - 1); }
+        else { e = rem >> 5; tt = rem & 31; }
+        const int r = r0 + tt;
+        if (r < nl) lv.tmp[(size_t)c * n3 + eaddr<AXIS>(n, lg, r, e)] = tl[(c * n + e) * TS + tt];
+      }
+    } else {
+      // Adam (PyTorch semantics) on the vertices of these x-lines
+      const float b1f = J.beta1, b2f = J.beta2;
+      const float step = lv.lr * J.bias[0];
+      const float ib2 = J.bias[1];
+      for (int idx = threadIdx.x; idx < TILE_LINES * n; idx += SOB_THREADS) {
+        const int tt = idx >> lg, x = idx & (n - 1);
+        const int r = r0 + tt;
+        if (r >= nl) continue;
+        const int v = (r << lg) + x;
+        float4 th = lv.theta[v];
+        float* thc = &th.x;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float g = tl[(c * n + x) * TS + tt];
+          if (J.keep_pgrad) lv.tmp[(size_t)c * n3 + v] = g;
+          float m = lv.m[(size_t)c * n3 + v], vv = lv.v[(size_t)c * n3 + v];
+          m = b1f * m + (1.f - b1f) * g;
+          vv = b2f * vv + (1.f - b2f) * g * g;
+          lv.m[(size_t)c * n3 + v] = m;
+          lv.v[(size_t)c * n3 + v] = vv;
+          thc[c] -= step * m / (sqrtf(vv) * ib2 + J.eps);
+        }
+        lv.theta[v] = th;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+void sobolev_configure() {
+  const int smem = sobolev_smem_bytes(256);
+  cudaFuncSetAttribute(k_sob<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_sob<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_sob<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_sob<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_sob<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+void launch_sobolev(const Plan* P, int grid, int nmax, cudaStream_t s) {
+  const int smem = sobolev_smem_bytes(nmax);
+  k_sob<1><<<grid, SOB_THREADS, smem, s>>>(P);
+  k_sob<2><<<grid, SOB_THREADS, smem, s>>>(P);
+  k_sob<3><<<grid, SOB_THREADS, smem, s>>>(P);
+  k_sob<4><<<grid, SOB_THREADS, smem, s>>>(P);
+  k_sob<5><<<grid, SOB_THREADS, smem, s>>>(P);
+}
+
+}  // namespace pdg

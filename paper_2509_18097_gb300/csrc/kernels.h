@@ -1,0 +1,48 @@
+// Host-side launchers of the libpdg kernels (each defined next to its kernels).
+#pragma once
+#include "pdg_internal.cuh"
+
+namespace pdg {
+
+// per step (plan-driven; `grid` = blocks of the persistent launch)
+void launch_plan(Plan* P, int bump, cudaStream_t s);
+void launch_interp(const Plan* P, int grid, cudaStream_t s);
+void launch_mov_scan(const Plan* P, int grid, cudaStream_t s);
+void launch_mov_scatter(const Plan* P, int grid, cudaStream_t s);
+void launch_nn(const Plan* P, int grid, cudaStream_t s);
+void launch_nn_hard(const Plan* P, int grid, cudaStream_t s);
+void launch_iso_edges(const Plan* P, int grid, cudaStream_t s);
+void launch_assemble(const Plan* P, int grid, cudaStream_t s);
+void launch_adjoint(const Plan* P, int grid, cudaStream_t s);
+void launch_sobolev(const Plan* P, int grid, int nmax, cudaStream_t s);
+void launch_loss(const Plan* P, int grid, cudaStream_t s);
+
+// per frame / per call (one job)
+void launch_pack4(const float* in, float4* out, int n, cudaStream_t s);
+void launch_unpack4(const float4* in, float* out, int n, cudaStream_t s);
+void launch_check_finite(const float* in, int n, int* flag, cudaStream_t s);
+void launch_frame_points(Job* J, int Q, int E, cudaStream_t s);
+void launch_tgt_build(Job* J, const Job& hJ, cudaStream_t s);
+void launch_csr_build(Job* J, const Job& hJ, cudaStream_t s);
+void launch_end_frame(Job* J, int V, cudaStream_t s);
+void launch_deform(const Job* J, const float* in, float* out, int n, cudaStream_t s);
+
+// generic exclusive scans over explicit segments (per-frame structures)
+struct ScanSeg {
+  const int* in;
+  int* out;   // [len + 1]
+  int len;
+  int* csum;  // [ceil(len / SCAN_CHUNK)]
+};
+void launch_scan_segments(const ScanSeg* hsegs, int nseg, ScanSeg* dsegs_scratch, int* dpre_scratch,
+                          cudaStream_t s);
+
+int sobolev_smem_bytes(int n);
+void sobolev_configure();
+
+// misc conversions
+void launch_soa_to_aos(const float* in, float* out, int n3, cudaStream_t s);
+void launch_aos_to_float4(const float* in, float4* out, int n, cudaStream_t s);
+void launch_copy_int(const int* in, int* out, int n, cudaStream_t s);
+
+}  // namespace pdg

@@ -1,0 +1,160 @@
+// Internal device-side data structures and helpers shared by the kernels and the host
+// runtime of libpdg (Preconditioned Deformation Grids, arXiv 2509.18097).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pdg.h"
+
+namespace pdg {
+
+constexpr int MAXJ = 256;            // jobs (contexts) per batch
+constexpr int MAXL = PDG_MAX_LEVELS; // grid levels
+constexpr int SCAN_CHUNK = 4096;     // elements per scan chunk (1024 threads x 4)
+constexpr int SCAN_THREADS = 1024;
+constexpr int TILE_LINES = 32;       // lines per Sobolev tile (per channel)
+constexpr int SOB_WARPS = 8;
+constexpr int SOB_THREADS = SOB_WARPS * 32;
+constexpr int NN_RMAX = 8;           // ring radius after which a query is searched exhaustively
+constexpr double FX_SCALE = 1099511627776.0;  // 2^40: fixed-point scale of the reverse Chamfer sums
+
+// A uniform cell grid over the domain used by the exact nearest-neighbour search.
+// G = 2^bits cells per axis.  Keys are (interleave(cy, cz) << bits) | cx, so the cells of
+// one x-row are contiguous and rows follow a 2-D Morton order in (y, z).  A grid may hold
+// `nsets` point sets in one key space (set s occupies keys [s G^3, (s+1) G^3)).
+struct CellGrid {
+  int bits;
+  int nsets;
+  float lo[3];
+  float inv_h[3];  // G / (hi - lo)
+  float h[3];      // (hi - lo) / G
+  int* hist;       // [nsets G^3] per-cell counts; all zero between builds
+  int* off;        // [nsets G^3 + 1] exclusive prefix of hist
+  int* keys;       // [points] key of each point (scratch of the build)
+  float4* pts;     // [points] points sorted by key; .w = original index (int bits)
+  int* csum;       // scan chunk sums scratch
+};
+
+struct Level {
+  int n;       // vertices per axis (1 or a power of two)
+  int lg;      // log2(n)
+  int n3;      // n^3
+  int tiles;   // Sobolev tiles: ceil(n^2 / 32)
+  float lr;    // learning rate of the level (already x0.1 without preconditioning)
+  float lam;   // lambda of the level
+  float4* theta;  // [n3] values (x, y, z, 0)
+  float* m;       // [3][n3] Adam first moment
+  float* v;       // [3][n3] Adam second moment
+  float* g;       // [3][n3] dLoss/dTheta (zero at vertices no point touches)
+  float* tmp;     // [3][n3] spectral work array (and preconditioned gradient in debug mode)
+  float* mu;      // [n] eigenvalues 4 sin^2(pi k / 2n) of the 1-D path Laplacian
+  float2* tw;     // [n/2] FFT twiddles exp(-2 pi i k / n)
+  float2* tw4;    // [n] DCT twiddles exp(-i pi k / 2n)
+  // point -> vertex interpolation lists, built once per frame (x is fixed in a frame)
+  int* cnt;       // [n3] per-vertex entry counts (zero between builds)
+  int* rowptr;    // [n3 + 1]
+  int* flag;      // [n3 + 1] active-vertex flags, then their exclusive prefix
+  int* act_v;     // [cap] active vertices (ascending)
+  int* act_ptr;   // [cap + 1] entry range of each active vertex
+  int* ent_p;     // [8 Q] point of each entry
+  float* ent_w;   // [8 Q] trilinear weight / L
+  int* n_active;  // device scalar
+  int* csum;      // scan scratch
+};
+
+struct Job {
+  int L;
+  Level lev[MAXL];
+  float lo[3], hi[3];
+  float alpha, w_mesh, w_pts, w_iso;
+  int stopgrad, precondition, keep_pgrad;
+  float beta1, beta2, eps;
+  int V, N, M, E, Q;       // template verts, source pts, target pts, edges, V + N
+  int max_pts;
+  float4* x;               // [Q] undeformed query points (template first), fixed in a frame
+  float4* y;               // [Q] deformed points
+  float4* gfwd;            // [Q] forward Chamfer gradient
+  long long* acc;          // [Q][3] reverse Chamfer sums, fixed point (2^-40)
+  float4* gy;              // [Q] dLoss/dy
+  float* loss_fwd;         // [Q] phi(d^2) of each forward query
+  float* loss_rev;         // [2 max_pts] phi(d^2) of each reverse query (set 0 then set 1)
+  float* loss_iso;         // [E] |r_e|
+  int* nn_fwd;             // [Q]
+  int* nn_rev;             // [2 max_pts]
+  float4* edge_d;          // [E] sgn(r) (y_i - y_j) / (|y_i - y_j| E)
+  const int2* edges;       // [E]
+  float* e_prev;           // [E] rest lengths from X_{t-1}
+  const int* v2e_ptr;      // [V + 1]
+  const int* v2e;          // [2E] (edge << 1) | (1 if the vertex is the edge's second end)
+  float4* src4;            // [max_pts] current source cloud P_{t-1}
+  float4* tgt4;            // [max_pts] target P_t
+  float4* verts4;          // [V] current deformed template X_{t-1}
+  CellGrid tgt;            // target grid, one set, built per frame
+  CellGrid mov;            // moving grid, two sets (template, source), rebuilt every step
+  int* hard;               // [Q + 2 max_pts] queries left by the one-ring search
+  int* hard_count;         // device scalar
+  int* step;               // Adam step count k
+  float* bias;             // [2] 1 / (1 - beta1^k), 1 / sqrt(1 - beta2^k) of the current step
+  double* loss;            // [4] total, cd_mesh, cd_pts, iso of the last step
+  int* status;             // sticky error flags (1: non-finite loss)
+};
+
+enum Stage { ST_Q = 0, ST_NNQ, ST_E, ST_MOVCH, ST_ADJ, ST_TILE, ST_JOB, NSTAGE };
+
+struct Plan {
+  int n_jobs;
+  int pad_[3];
+  Job* jobs[MAXJ];
+  int pre[NSTAGE][MAXJ + 1];
+};
+
+// ------------------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ int find_job(const int* pre, int n_jobs, int item) {
+  int lo = 0, hi = n_jobs;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (__ldg(pre + mid) <= item) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__host__ __device__ __forceinline__ uint32_t part1by1(uint32_t v) {
+  v &= 0xFFu;
+  v = (v | (v << 4)) & 0x0F0Fu;
+  v = (v | (v << 2)) & 0x3333u;
+  v = (v | (v << 1)) & 0x5555u;
+  return v;
+}
+
+__host__ __device__ __forceinline__ int row_key(int cy, int cz, int bits) {
+  return (int)((part1by1((uint32_t)cy) | (part1by1((uint32_t)cz) << 1)) << bits);
+}
+
+__device__ __forceinline__ int cell_coord(float p, float lo, float inv_h, int G) {
+  float t = (p - lo) * inv_h;
+  t = fminf(fmaxf(t, -1.0f), (float)G);
+  int c = (int)floorf(t);
+  return min(max(c, 0), G - 1);
+}
+
+__device__ __forceinline__ int cell_key(const CellGrid& g, float x, float y, float z, int set) {
+  int G = 1 << g.bits;
+  int cx = cell_coord(x, g.lo[0], g.inv_h[0], G);
+  int cy = cell_coord(y, g.lo[1], g.inv_h[1], G);
+  int cz = cell_coord(z, g.lo[2], g.inv_h[2], G);
+  return set * (G * G * G) + row_key(cy, cz, g.bits) + cx;
+}
+
+// squared distance, difference form; the same expression everywhere so that candidate
+// comparisons are consistent between kernels
+__device__ __forceinline__ float sqdist(float ax, float ay, float az, float bx, float by, float bz) {
+  const float dx = __fsub_rn(ax, bx), dy = __fsub_rn(ay, by), dz = __fsub_rn(az, bz);
+  return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+
+__device__ __forceinline__ long long to_fx(float v) { return __float2ll_rn(v * 1099511627776.0f); }
+__device__ __forceinline__ float from_fx(long long a) { return __ll2float_rn(a) * (1.0f / 1099511627776.0f); }
+
+}  // namespace pdg

@@ -1,0 +1,933 @@
+// Host runtime and C ABI of libpdg: per-sequence contexts (one device arena each),
+// per-frame set-up, the CUDA-graph step, batching of contexts into one graph, and
+// checkpoint/resume.  See include/pdg.h for the contract of every entry point.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+
+using namespace pdg;
+
+namespace {
+
+constexpr double PI = 3.14159265358979323846;
+
+struct Arena {
+  size_t off = 0;
+  template <class T>
+  size_t take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    const size_t at = off;
+    off += count * sizeof(T);
+    return at;
+  }
+};
+
+int grid_bits(long count) {
+  const double g = std::sqrt(std::max(count, 1L) / 8.0);
+  int b = (int)std::lround(std::log2(std::max(g, 1.0)));
+  return std::min(std::max(b, 2), 7);
+}
+
+bool valid_res(int n) { return n == 1 || (n >= 2 && n <= 256 && (n & (n - 1)) == 0); }
+
+int ilog2(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------------------- context
+
+struct pdg_ctx {
+  pdg_config cfg{};
+  int dev = 0, sms = 1;
+  int V = 0, E = 0, max_pts = 0, Qmax = 0;
+  bool in_frame = false;
+  int steps_in_frame = 0;
+  std::string err;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  Job h{};                 // host mirror of the device job struct
+  Job* dJ = nullptr;       // device job struct (inside the arena)
+  Plan* dplan = nullptr;   // device plan holding only this job
+  int* dflag = nullptr;
+  float* stage = nullptr;  // [stage_pts][3] staging of host inputs
+  int stage_pts = 0;
+  int nmax = 1;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<int> v2e_ptr, v2e;
+
+  pdg_status fail(pdg_status s, const std::string& m) {
+    err = m;
+    return s;
+  }
+  pdg_status cuda(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return PDG_OK;
+    err = std::string(what) + ": " + cudaGetErrorString(e);
+    return PDG_ERR_CUDA;
+  }
+};
+
+struct pdg_batch {
+  int max_jobs = 0;
+  int n = 0;
+  std::vector<pdg_ctx*> members;
+  Plan* dplan = nullptr;
+  Plan* hplan = nullptr;  // pinned host copy
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int graph_nmax = 0;
+  bool dirty = true;  // membership changed since the last upload of the job table
+  std::string err;
+};
+
+#define TRY(expr)                                  \
+  do {                                             \
+    pdg_status _s = (expr);                        \
+    if (_s != PDG_OK) return _s;                   \
+  } while (0)
+#define CU(ctx, call) TRY((ctx)->cuda((call), #call))
+
+namespace {
+
+// sizes of every buffer of a context (used by pdg_query_bytes and pdg_create)
+struct Layout {
+  size_t total = 0;
+  size_t job, plan, flag, stage;
+  struct Lv {
+    size_t theta, m, v, g, tmp, mu, tw, tw4, cnt, rowptr, flag, act_v, act_ptr, ent_p, ent_w, n_active, csum;
+    int cap;
+  } lv[MAXL];
+  size_t x, y, gfwd, gy, acc, loss_fwd, loss_rev, loss_iso, nn_fwd, nn_rev, edge_d, edges, e_prev, v2e_ptr, v2e;
+  size_t src4, tgt4, verts4;
+  size_t t_hist, t_off, t_keys, t_pts, t_csum, m_hist, m_off, m_keys, m_pts, m_csum;
+  size_t hard, hard_count, step, bias, loss, status;
+  int tbits, mbits;
+};
+
+Layout make_layout(const pdg_config& c, int V, int E, int max_pts) {
+  Layout L;
+  Arena a;
+  const int Q = V + max_pts;
+  L.job = a.take<Job>(1);
+  L.plan = a.take<Plan>(1);
+  L.flag = a.take<int>(4);
+  const int sp = std::max(V, max_pts);
+  L.stage = a.take<float>(3 * (size_t)sp);
+  for (int l = 0; l < c.n_levels; ++l) {
+    const size_t n = c.res[l], n3 = n * n * n;
+    auto& v = L.lv[l];
+    v.cap = (int)std::min<size_t>(n3, 8 * (size_t)Q);
+    v.theta = a.take<float4>(n3);
+    v.m = a.take<float>(3 * n3);
+    v.v = a.take<float>(3 * n3);
+    v.g = a.take<float>(3 * n3);
+    v.tmp = a.take<float>(3 * n3);
+    v.mu = a.take<float>(n);
+    v.tw = a.take<float2>(std::max<size_t>(n / 2, 1));
+    v.tw4 = a.take<float2>(n);
+    v.cnt = a.take<int>(n3);
+    v.rowptr = a.take<int>(n3 + 1);
+    v.flag = a.take<int>(n3 + 1);
+    v.act_v = a.take<int>(v.cap);
+    v.act_ptr = a.take<int>(v.cap + 1);
+    v.ent_p = a.take<int>(8 * (size_t)Q);
+    v.ent_w = a.take<float>(8 * (size_t)Q);
+    v.n_active = a.take<int>(1);
+    v.csum = a.take<int>((n3 + 1) / SCAN_CHUNK + 2);
+  }
+  L.x = a.take<float4>(Q);
+  L.y = a.take<float4>(Q);
+  L.gfwd = a.take<float4>(Q);
+  L.gy = a.take<float4>(Q);
+  L.acc = a.take<long long>(3 * (size_t)Q);
+  L.loss_fwd = a.take<float>(Q);
+  L.loss_rev = a.take<float>(2 * (size_t)max_pts);
+  L.loss_iso = a.take<float>(std::max(E, 1));
+  L.nn_fwd = a.take<int>(Q);
+  L.nn_rev = a.take<int>(2 * (size_t)max_pts);
+  L.edge_d = a.take<float4>(std::max(E, 1));
+  L.edges = a.take<int2>(std::max(E, 1));
+  L.e_prev = a.take<float>(std::max(E, 1));
+  L.v2e_ptr = a.take<int>(V + 1);
+  L.v2e = a.take<int>(std::max(2 * E, 1));
+  L.src4 = a.take<float4>(max_pts);
+  L.tgt4 = a.take<float4>(max_pts);
+  L.verts4 = a.take<float4>(V);
+  L.tbits = grid_bits(max_pts);
+  L.mbits = grid_bits(std::max(V, max_pts));
+  const size_t tG3 = size_t(1) << (3 * L.tbits), mG3 = size_t(1) << (3 * L.mbits);
+  L.t_hist = a.take<int>(tG3);
+  L.t_off = a.take<int>(tG3 + 1);
+  L.t_keys = a.take<int>(max_pts);
+  L.t_pts = a.take<float4>(max_pts);
+  L.t_csum = a.take<int>(tG3 / SCAN_CHUNK + 2);
+  L.m_hist = a.take<int>(2 * mG3);
+  L.m_off = a.take<int>(2 * mG3 + 1);
+  L.m_keys = a.take<int>(Q);
+  L.m_pts = a.take<float4>(Q);
+  L.m_csum = a.take<int>(2 * mG3 / SCAN_CHUNK + 2);
+  L.hard = a.take<int>(Q + 2 * (size_t)max_pts);
+  L.hard_count = a.take<int>(1);
+  L.step = a.take<int>(1);
+  L.bias = a.take<float>(2);
+  L.loss = a.take<double>(4);
+  L.status = a.take<int>(1);
+  L.total = (a.off + 255) & ~size_t(255);
+  return L;
+}
+
+const char* check_config(const pdg_config* c) {
+  if (!c) return "config is NULL";
+  if (c->n_levels < 1 || c->n_levels > PDG_MAX_LEVELS) return "n_levels must be in 1..8";
+  for (int l = 0; l < c->n_levels; ++l)
+    if (!valid_res(c->res[l])) return "each res must be 1 or a power of two in 2..256";
+  for (int a = 0; a < 3; ++a)
+    if (!(std::isfinite(c->lo[a]) && std::isfinite(c->hi[a]) && c->hi[a] > c->lo[a])) return "domain must have lo < hi";
+  const float f[] = {c->alpha, c->w_chamfer_mesh, c->w_chamfer_pts, c->w_iso, c->lr0, c->lr_growth, c->lambda0,
+                     c->lambda_growth, c->beta1, c->beta2, c->eps};
+  for (float v : f)
+    if (!std::isfinite(v) || v < 0) return "config parameters must be finite and non-negative";
+  if (c->beta1 >= 1 || c->beta2 >= 1) return "beta1, beta2 must be < 1";
+  return nullptr;
+}
+
+// copies `n` xyz triples (host or device) into a float4 device array
+pdg_status load_points(pdg_ctx* c, const float* xyz, int n, float4* dst, cudaStream_t s, bool check) {
+  if (n <= 0) return PDG_OK;
+  const float* src = xyz;
+  if (!is_device_ptr(xyz)) {
+    if (n > c->stage_pts) return c->fail(PDG_ERR_BUDGET, "point count exceeds the context capacity");
+    CU(c, cudaMemcpyAsync(c->stage, xyz, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice, s));
+    src = c->stage;
+  }
+  if (check) {
+    CU(c, cudaMemsetAsync(c->dflag, 0, sizeof(int), s));
+    launch_check_finite(src, 3 * n, c->dflag, s);
+    int f = 0;
+    CU(c, cudaMemcpyAsync(&f, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(c, cudaStreamSynchronize(s));
+    if (f) return c->fail(PDG_ERR_INVALID, "input points contain NaN or Inf");
+  }
+  launch_pack4(src, dst, n, s);
+  return c->cuda(cudaGetLastError(), "pack points");
+}
+
+pdg_status upload_job(pdg_ctx* c, cudaStream_t s) {
+  CU(c, cudaMemcpyAsync(c->dJ, &c->h, sizeof(Job), cudaMemcpyHostToDevice, s));
+  return PDG_OK;
+}
+
+// The step as an explicit list of stages; the graph capture and the profiling path launch
+// exactly the same sequence.
+const char* const STAGE_NAMES[] = {"plan",    "interp",     "mov_scan",  "mov_scatter", "nn",
+                                   "nn_hard", "iso_edges",  "assemble",  "adjoint",     "sobolev",
+                                   "loss"};
+constexpr int N_STAGES = sizeof(STAGE_NAMES) / sizeof(STAGE_NAMES[0]);
+
+void launch_stage(int i, const Plan* plan, int nmax, int sms, cudaStream_t s) {
+  const int grid = sms * 8;
+  const int smem = sobolev_smem_bytes(nmax);
+  const int tiles_per_sm = std::max(1, std::min(4, (227 * 1024) / std::max(smem, 1)));
+  switch (i) {
+    case 0: launch_plan(const_cast<Plan*>(plan), 1, s); break;
+    case 1: launch_interp(plan, grid, s); break;
+    case 2: launch_mov_scan(plan, sms * 2, s); break;
+    case 3: launch_mov_scatter(plan, grid, s); break;
+    case 4: launch_nn(plan, grid, s); break;
+    case 5: launch_nn_hard(plan, sms * 4, s); break;
+    case 6: launch_iso_edges(plan, grid, s); break;
+    case 7: launch_assemble(plan, grid, s); break;
+    case 8: launch_adjoint(plan, grid, s); break;
+    case 9: launch_sobolev(plan, sms * tiles_per_sm, nmax, s); break;
+    case 10: launch_loss(plan, std::min(sms, MAXJ), s); break;
+  }
+}
+
+pdg_status capture_step(pdg_ctx* c, const Plan* plan, int nmax, cudaStream_t cap, cudaGraphExec_t* out,
+                        std::string* err, int sms) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    *err = std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e);
+    return PDG_ERR_CUDA;
+  }
+  for (int i = 0; i < N_STAGES; ++i) launch_stage(i, plan, nmax, sms, cap);
+  e = cudaStreamEndCapture(cap, &g);
+  if (e != cudaSuccess) {
+    *err = std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e);
+    if (g) cudaGraphDestroy(g);
+    return PDG_ERR_CUDA;
+  }
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    *err = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e);
+    return PDG_ERR_CUDA;
+  }
+  (void)c;
+  return PDG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pdg_config_default(pdg_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->n_levels = 4;
+  c->res[0] = 16;
+  c->res[1] = 32;
+  c->res[2] = 64;
+  c->res[3] = 128;
+  for (int a = 0; a < 3; ++a) {
+    c->lo[a] = -1.5f;
+    c->hi[a] = 1.5f;
+  }
+  c->alpha = 5.56f;
+  c->w_chamfer_mesh = 1.f;
+  c->w_chamfer_pts = 1.f;
+  c->w_iso = 250.f;
+  c->lr0 = 5e-3f;
+  c->lr_growth = 1.1f;
+  c->lambda0 = 0.25f;
+  c->lambda_growth = 1.5f;
+  c->beta1 = 0.9f;
+  c->beta2 = 0.999f;
+  c->eps = 1e-8f;
+  c->precondition = 1;
+  c->robust_weight_stopgrad = 0;
+  c->warm_start = 0;
+}
+
+size_t pdg_query_bytes(const pdg_config* cfg, int n_verts, int n_edges, int max_pts) {
+  if (check_config(cfg) || n_verts < 1 || n_edges < 0 || max_pts < 1) return 0;
+  return make_layout(*cfg, n_verts, n_edges, max_pts).total;
+}
+
+const char* pdg_status_string(pdg_status s) {
+  switch (s) {
+    case PDG_OK: return "ok";
+    case PDG_ERR_INVALID: return "invalid argument";
+    case PDG_ERR_OOM: return "out of device memory";
+    case PDG_ERR_BUDGET: return "over budget or capacity";
+    case PDG_ERR_CUDA: return "CUDA error";
+    case PDG_ERR_NONFINITE: return "non-finite loss";
+    case PDG_ERR_TIMEOUT: return "device wait timed out";
+    case PDG_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char* pdg_last_error(const pdg_ctx* c) { return c ? c->err.c_str() : "context is NULL"; }
+
+void pdg_destroy(pdg_ctx* c) {
+  if (!c) return;
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->arena) cudaFree(c->arena);
+  delete c;
+}
+
+pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_verts, const int32_t* edges,
+                      int n_edges, const float* source_xyz, int n_src, int max_pts, void* cuda_stream,
+                      pdg_ctx** out) {
+  if (!out) return PDG_ERR_INVALID;
+  *out = nullptr;
+  if (check_config(cfg) || !template_xyz || !source_xyz || n_verts < 1 || n_src < 1 || max_pts < n_src ||
+      n_edges < 0 || (n_edges > 0 && !edges))
+    return PDG_ERR_INVALID;
+  if ((long)n_verts + max_pts > (1L << 29) || (long)n_edges > (1L << 28)) return PDG_ERR_BUDGET;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  pdg_ctx* c = new pdg_ctx();
+  c->cfg = *cfg;
+  c->V = n_verts;
+  c->E = n_edges;
+  c->max_pts = max_pts;
+  c->Qmax = n_verts + max_pts;
+  auto bail = [&](pdg_status st) {
+    pdg_destroy(c);
+    return st;
+  };
+  if (cudaGetDevice(&c->dev) != cudaSuccess) return bail(PDG_ERR_CUDA);
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->dev);
+  sobolev_configure();
+
+  // edges to the host (validation + vertex -> edge lists)
+  std::vector<int32_t> he(2 * (size_t)n_edges);
+  if (n_edges) {
+    if (is_device_ptr(edges)) {
+      if (cudaMemcpy(he.data(), edges, he.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess) return bail(PDG_ERR_CUDA);
+    } else {
+      std::memcpy(he.data(), edges, he.size() * 4);
+    }
+  }
+  for (size_t i = 0; i < he.size(); ++i)
+    if (he[i] < 0 || he[i] >= n_verts) return bail(PDG_ERR_INVALID);
+  c->v2e_ptr.assign(n_verts + 1, 0);
+  for (int e = 0; e < n_edges; ++e) {
+    c->v2e_ptr[he[2 * e] + 1]++;
+    c->v2e_ptr[he[2 * e + 1] + 1]++;
+  }
+  for (int v = 0; v < n_verts; ++v) c->v2e_ptr[v + 1] += c->v2e_ptr[v];
+  c->v2e.assign(std::max(2 * n_edges, 1), 0);
+  {
+    std::vector<int> fill(c->v2e_ptr.begin(), c->v2e_ptr.end() - 1);
+    for (int e = 0; e < n_edges; ++e) {  // ascending edge order within each vertex
+      c->v2e[fill[he[2 * e]]++] = e << 1;
+      c->v2e[fill[he[2 * e + 1]]++] = (e << 1) | 1;
+    }
+  }
+
+  const Layout L = make_layout(*cfg, n_verts, n_edges, max_pts);
+  if (cudaMalloc(&c->arena, L.total) != cudaSuccess) {
+    cudaGetLastError();
+    c->arena = nullptr;
+    return bail(PDG_ERR_OOM);
+  }
+  c->arena_bytes = L.total;
+  if (cudaMemsetAsync(c->arena, 0, L.total, s) != cudaSuccess) return bail(PDG_ERR_CUDA);
+  char* A = c->arena;
+  auto P = [&](size_t off) { return (void*)(A + off); };
+  Job& J = c->h;
+  std::memset(&J, 0, sizeof(J));
+  J.L = cfg->n_levels;
+  for (int a = 0; a < 3; ++a) {
+    J.lo[a] = cfg->lo[a];
+    J.hi[a] = cfg->hi[a];
+  }
+  J.alpha = cfg->alpha;
+  J.w_mesh = cfg->w_chamfer_mesh;
+  J.w_pts = cfg->w_chamfer_pts;
+  J.w_iso = cfg->w_iso;
+  J.stopgrad = cfg->robust_weight_stopgrad ? 1 : 0;
+  J.precondition = cfg->precondition ? 1 : 0;
+  J.beta1 = cfg->beta1;
+  J.beta2 = cfg->beta2;
+  J.eps = cfg->eps;
+  J.V = n_verts;
+  J.N = n_src;
+  J.M = 1;
+  J.E = n_edges;
+  J.Q = n_verts + n_src;
+  J.max_pts = max_pts;
+  c->dJ = (Job*)P(L.job);
+  c->dplan = (Plan*)P(L.plan);
+  c->dflag = (int*)P(L.flag);
+  c->stage = (float*)P(L.stage);
+  c->stage_pts = std::max(n_verts, max_pts);
+  std::vector<float> mu;
+  std::vector<float2> tw, tw4;
+  for (int l = 0; l < J.L; ++l) {
+    Level& lv = J.lev[l];
+    const auto& o = L.lv[l];
+    const int n = cfg->res[l];
+    lv.n = n;
+    lv.lg = ilog2(n);
+    lv.n3 = n * n * n;
+    lv.tiles = (n * n + TILE_LINES - 1) / TILE_LINES;
+    lv.lr = (float)(cfg->lr0 * std::pow((double)cfg->lr_growth, l) * (cfg->precondition ? 1.0 : 0.1));
+    lv.lam = (float)(cfg->lambda0 * std::pow((double)cfg->lambda_growth, l));
+    lv.theta = (float4*)P(o.theta);
+    lv.m = (float*)P(o.m);
+    lv.v = (float*)P(o.v);
+    lv.g = (float*)P(o.g);
+    lv.tmp = (float*)P(o.tmp);
+    lv.mu = (float*)P(o.mu);
+    lv.tw = (float2*)P(o.tw);
+    lv.tw4 = (float2*)P(o.tw4);
+    lv.cnt = (int*)P(o.cnt);
+    lv.rowptr = (int*)P(o.rowptr);
+    lv.flag = (int*)P(o.flag);
+    lv.act_v = (int*)P(o.act_v);
+    lv.act_ptr = (int*)P(o.act_ptr);
+    lv.ent_p = (int*)P(o.ent_p);
+    lv.ent_w = (float*)P(o.ent_w);
+    lv.n_active = (int*)P(o.n_active);
+    lv.csum = (int*)P(o.csum);
+    c->nmax = std::max(c->nmax, n);
+    mu.resize(n);
+    tw.resize(std::max(n / 2, 1));
+    tw4.resize(n);
+    for (int k = 0; k < n; ++k) {
+      const double sk = std::sin(PI * k / (2.0 * n));
+      mu[k] = (float)(4.0 * sk * sk);
+      tw4[k] = make_float2((float)std::cos(PI * k / (2.0 * n)), (float)-std::sin(PI * k / (2.0 * n)));
+    }
+    for (int k = 0; k < std::max(n / 2, 1); ++k)
+      tw[k] = make_float2((float)std::cos(2 * PI * k / n), (float)-std::sin(2 * PI * k / n));
+    // pageable sources are staged before the call returns, so the vectors may be reused
+    if (cudaMemcpyAsync(lv.mu, mu.data(), n * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(lv.tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(lv.tw4, tw4.data(), n * sizeof(float2), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return bail(PDG_ERR_CUDA);
+  }
+  J.x = (float4*)P(L.x);
+  J.y = (float4*)P(L.y);
+  J.gfwd = (float4*)P(L.gfwd);
+  J.gy = (float4*)P(L.gy);
+  J.acc = (long long*)P(L.acc);
+  J.loss_fwd = (float*)P(L.loss_fwd);
+  J.loss_rev = (float*)P(L.loss_rev);
+  J.loss_iso = (float*)P(L.loss_iso);
+  J.nn_fwd = (int*)P(L.nn_fwd);
+  J.nn_rev = (int*)P(L.nn_rev);
+  J.edge_d = (float4*)P(L.edge_d);
+  J.edges = (const int2*)P(L.edges);
+  J.e_prev = (float*)P(L.e_prev);
+  J.v2e_ptr = (const int*)P(L.v2e_ptr);
+  J.v2e = (const int*)P(L.v2e);
+  J.src4 = (float4*)P(L.src4);
+  J.tgt4 = (float4*)P(L.tgt4);
+  J.verts4 = (float4*)P(L.verts4);
+  auto grid_init = [&](CellGrid& g, int bits, int nsets, size_t hist, size_t off, size_t keys, size_t pts, size_t csum) {
+    g.bits = bits;
+    g.nsets = nsets;
+    const int G = 1 << bits;
+    for (int a = 0; a < 3; ++a) {
+      g.lo[a] = cfg->lo[a];
+      g.inv_h[a] = (float)(G / ((double)cfg->hi[a] - cfg->lo[a]));
+      g.h[a] = (float)(((double)cfg->hi[a] - cfg->lo[a]) / G);
+    }
+    g.hist = (int*)P(hist);
+    g.off = (int*)P(off);
+    g.keys = (int*)P(keys);
+    g.pts = (float4*)P(pts);
+    g.csum = (int*)P(csum);
+  };
+  grid_init(J.tgt, L.tbits, 1, L.t_hist, L.t_off, L.t_keys, L.t_pts, L.t_csum);
+  grid_init(J.mov, L.mbits, 2, L.m_hist, L.m_off, L.m_keys, L.m_pts, L.m_csum);
+  J.hard = (int*)P(L.hard);
+  J.hard_count = (int*)P(L.hard_count);
+  J.step = (int*)P(L.step);
+  J.bias = (float*)P(L.bias);
+  J.loss = (double*)P(L.loss);
+  J.status = (int*)P(L.status);
+
+  if (n_edges) {
+    if (cudaMemcpyAsync((void*)J.edges, he.data(), he.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync((void*)J.v2e, c->v2e.data(), c->v2e.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return bail(PDG_ERR_CUDA);
+  }
+  if (cudaMemcpyAsync((void*)J.v2e_ptr, c->v2e_ptr.data(), c->v2e_ptr.size() * 4, cudaMemcpyHostToDevice, s) !=
+      cudaSuccess)
+    return bail(PDG_ERR_CUDA);
+  if (load_points(c, template_xyz, n_verts, J.verts4, s, true) != PDG_OK) {
+    const pdg_status st = c->err.find("NaN") != std::string::npos ? PDG_ERR_INVALID : PDG_ERR_CUDA;
+    return bail(st);
+  }
+  if (load_points(c, source_xyz, n_src, J.src4, s, true) != PDG_OK) {
+    const pdg_status st = c->err.find("NaN") != std::string::npos ? PDG_ERR_INVALID : PDG_ERR_CUDA;
+    return bail(st);
+  }
+  if (upload_job(c, s) != PDG_OK) return bail(PDG_ERR_CUDA);
+  {
+    Plan hp;
+    std::memset(&hp, 0, sizeof(hp));
+    hp.n_jobs = 1;
+    hp.jobs[0] = c->dJ;
+    if (cudaMemcpyAsync(c->dplan, &hp, sizeof(Plan), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return bail(PDG_ERR_CUDA);
+  }
+  if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) return bail(PDG_ERR_CUDA);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return bail(PDG_ERR_CUDA);
+  *out = c;
+  return PDG_OK;
+}
+
+pdg_status pdg_set_debug(pdg_ctx* c, int keep_pgrad) {
+  if (!c) return PDG_ERR_INVALID;
+  c->h.keep_pgrad = keep_pgrad ? 1 : 0;
+  return upload_job(c, 0) == PDG_OK ? c->cuda(cudaDeviceSynchronize(), "set_debug") : PDG_ERR_CUDA;
+}
+
+pdg_status pdg_begin_frame(pdg_ctx* c, const float* target_xyz, int n_tgt, void* cuda_stream) {
+  if (!c) return PDG_ERR_INVALID;
+  if (c->in_frame) return c->fail(PDG_ERR_STATE, "a frame is already open");
+  if (!target_xyz || n_tgt < 1) return c->fail(PDG_ERR_INVALID, "empty target");
+  if (n_tgt > c->max_pts) return c->fail(PDG_ERR_BUDGET, "target larger than max_pts");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  Job& J = c->h;
+  TRY(load_points(c, target_xyz, n_tgt, J.tgt4, s, true));
+  J.M = n_tgt;
+  J.Q = J.V + J.N;
+  TRY(upload_job(c, s));
+  launch_frame_points(c->dJ, J.Q, J.E, s);
+  for (int l = 0; l < J.L; ++l) {
+    const Level& lv = J.lev[l];
+    if (!c->cfg.warm_start) CU(c, cudaMemsetAsync(lv.theta, 0, sizeof(float4) * lv.n3, s));
+    CU(c, cudaMemsetAsync(lv.m, 0, sizeof(float) * 3 * lv.n3, s));
+    CU(c, cudaMemsetAsync(lv.v, 0, sizeof(float) * 3 * lv.n3, s));
+    CU(c, cudaMemsetAsync(lv.g, 0, sizeof(float) * 3 * lv.n3, s));
+  }
+  CU(c, cudaMemsetAsync(J.step, 0, sizeof(int), s));
+  CU(c, cudaMemsetAsync(J.status, 0, sizeof(int), s));
+  CU(c, cudaMemsetAsync(J.loss, 0, 4 * sizeof(double), s));
+  launch_tgt_build(c->dJ, J, s);
+  launch_csr_build(c->dJ, J, s);
+  CU(c, cudaGetLastError());
+  c->in_frame = true;
+  c->steps_in_frame = 0;
+  return PDG_OK;
+}
+
+pdg_status pdg_step(pdg_ctx* c, int n_steps, void* cuda_stream) {
+  if (!c) return PDG_ERR_INVALID;
+  if (!c->in_frame) return c->fail(PDG_ERR_STATE, "pdg_step outside a frame");
+  if (n_steps < 0) return c->fail(PDG_ERR_INVALID, "negative step count");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (!c->gexec) {
+    // the captured launches must not start before this stream's pending set-up
+    CU(c, cudaStreamSynchronize(s));
+    TRY(capture_step(c, c->dplan, c->nmax, c->cap, &c->gexec, &c->err, c->sms));
+  }
+  for (int i = 0; i < n_steps; ++i) CU(c, cudaGraphLaunch(c->gexec, s));
+  c->steps_in_frame += n_steps;
+  return PDG_OK;
+}
+
+int pdg_profile_stages(void) { return N_STAGES; }
+
+const char* pdg_profile_stage_name(int i) { return (i >= 0 && i < N_STAGES) ? STAGE_NAMES[i] : ""; }
+
+pdg_status pdg_profile_step(pdg_ctx* c, int n_steps, double* stage_ms, void* cuda_stream) {
+  if (!c || !stage_ms || n_steps < 0) return PDG_ERR_INVALID;
+  if (!c->in_frame) return c->fail(PDG_ERR_STATE, "pdg_profile_step outside a frame");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  cudaEvent_t ev[N_STAGES + 1];
+  for (auto& e : ev) CU(c, cudaEventCreate(&e));
+  for (int i = 0; i < N_STAGES; ++i) stage_ms[i] = 0.0;
+  pdg_status st = PDG_OK;
+  for (int k = 0; k < n_steps && st == PDG_OK; ++k) {
+    for (int i = 0; i < N_STAGES; ++i) {
+      cudaEventRecord(ev[i], s);
+      launch_stage(i, c->dplan, c->nmax, c->sms, s);
+    }
+    cudaEventRecord(ev[N_STAGES], s);
+    st = c->cuda(cudaEventSynchronize(ev[N_STAGES]), "profile step");
+    for (int i = 0; i < N_STAGES && st == PDG_OK; ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+      stage_ms[i] += ms;
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  c->steps_in_frame += n_steps;
+  return st;
+}
+
+pdg_status pdg_end_frame(pdg_ctx* c, pdg_fit_stats* stats, void* cuda_stream) {
+  if (!c) return PDG_ERR_INVALID;
+  if (!c->in_frame) return c->fail(PDG_ERR_STATE, "no open frame");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  Job& J = c->h;
+  launch_end_frame(c->dJ, J.V, s);
+  CU(c, cudaMemcpyAsync(J.src4, J.tgt4, sizeof(float4) * J.M, cudaMemcpyDeviceToDevice, s));
+  double loss[4];
+  int status = 0;
+  CU(c, cudaMemcpyAsync(loss, J.loss, sizeof(loss), cudaMemcpyDeviceToHost, s));
+  CU(c, cudaMemcpyAsync(&status, J.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CU(c, cudaStreamSynchronize(s));
+  J.N = J.M;
+  J.Q = J.V + J.N;
+  c->in_frame = false;
+  const pdg_status st = status ? PDG_ERR_NONFINITE : PDG_OK;
+  if (stats) {
+    stats->loss_total = loss[0];
+    stats->cd_mesh = loss[1];
+    stats->cd_pts = loss[2];
+    stats->iso = loss[3];
+    stats->n_steps = c->steps_in_frame;
+    stats->status = st;
+  }
+  if (st != PDG_OK) c->err = "a loss became NaN or Inf during the frame";
+  return st;
+}
+
+pdg_status pdg_fit_frame(pdg_ctx* c, const float* target_xyz, int n_tgt, int n_steps, pdg_fit_stats* stats,
+                         void* cuda_stream) {
+  TRY(pdg_begin_frame(c, target_xyz, n_tgt, cuda_stream));
+  const pdg_status st = pdg_step(c, n_steps, cuda_stream);
+  if (st != PDG_OK) {
+    c->in_frame = false;
+    return st;
+  }
+  return pdg_end_frame(c, stats, cuda_stream);
+}
+
+pdg_status pdg_deform(pdg_ctx* c, const float* xyz, int n, float* out, void* cuda_stream) {
+  if (!c) return PDG_ERR_INVALID;
+  if (n < 0 || (n > 0 && (!xyz || !out))) return c->fail(PDG_ERR_INVALID, "bad deform arguments");
+  if (n == 0) return PDG_OK;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const bool din = is_device_ptr(xyz), dout = is_device_ptr(out);
+  float* tmp = nullptr;
+  const size_t bytes = sizeof(float) * 3 * (size_t)n;
+  if (!din || !dout) CU(c, cudaMallocAsync((void**)&tmp, 2 * bytes, s));
+  const float* in = din ? xyz : tmp;
+  float* o = dout ? out : tmp + 3 * (size_t)n;
+  if (!din) CU(c, cudaMemcpyAsync(tmp, xyz, bytes, cudaMemcpyHostToDevice, s));
+  launch_deform(c->dJ, in, o, n, s);
+  if (!dout) CU(c, cudaMemcpyAsync(out, o, bytes, cudaMemcpyDeviceToHost, s));
+  if (tmp) CU(c, cudaFreeAsync(tmp, s));
+  if (!din || !dout) CU(c, cudaStreamSynchronize(s));
+  return c->cuda(cudaGetLastError(), "deform");
+}
+
+// copies `bytes` from a device buffer to `out` (host or device), synchronising for host
+static pdg_status copy_out(pdg_ctx* c, void* out, const void* dsrc, size_t bytes, cudaStream_t s) {
+  if (is_device_ptr(out)) {
+    CU(c, cudaMemcpyAsync(out, dsrc, bytes, cudaMemcpyDeviceToDevice, s));
+  } else {
+    CU(c, cudaMemcpyAsync(out, dsrc, bytes, cudaMemcpyDeviceToHost, s));
+    CU(c, cudaStreamSynchronize(s));
+  }
+  return PDG_OK;
+}
+
+pdg_status pdg_get_vertices(pdg_ctx* c, float* out, void* cuda_stream) {
+  if (!c || !out) return PDG_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const size_t bytes = sizeof(float) * 3 * (size_t)c->V;
+  float* tmp = nullptr;
+  CU(c, cudaMallocAsync((void**)&tmp, bytes, s));
+  launch_unpack4(c->h.verts4, tmp, c->V, s);
+  const pdg_status st = copy_out(c, out, tmp, bytes, s);
+  cudaFreeAsync(tmp, s);
+  return st;
+}
+
+pdg_status pdg_read(pdg_ctx* c, int which, int level, void* out, size_t out_bytes, void* cuda_stream) {
+  if (!c || !out) return PDG_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const Job& J = c->h;
+  const bool per_level = which == PDG_BUF_THETA || which == PDG_BUF_GRAD || which == PDG_BUF_PGRAD;
+  if (per_level && (level < 0 || level >= J.L)) return c->fail(PDG_ERR_INVALID, "bad level");
+  size_t need = 0;
+  switch (which) {
+    case PDG_BUF_THETA:
+    case PDG_BUF_GRAD:
+    case PDG_BUF_PGRAD: need = sizeof(float) * 3 * (size_t)J.lev[level].n3; break;
+    case PDG_BUF_Y:
+    case PDG_BUF_POINT_GRAD: need = sizeof(float) * 3 * (size_t)J.Q; break;
+    case PDG_BUF_NN_FWD: need = sizeof(int) * (size_t)J.Q; break;
+    case PDG_BUF_NN_REV: need = sizeof(int) * 2 * (size_t)J.M; break;
+    case PDG_BUF_LOSS: need = 4 * sizeof(double); break;
+    case PDG_BUF_SOURCE: need = sizeof(float) * 3 * (size_t)J.N; break;
+    default: return c->fail(PDG_ERR_INVALID, "unknown buffer");
+  }
+  if (out_bytes < need) return c->fail(PDG_ERR_INVALID, "output buffer too small");
+  if (which == PDG_BUF_PGRAD && !J.keep_pgrad) return c->fail(PDG_ERR_STATE, "call pdg_set_debug(ctx, 1) first");
+  if (which == PDG_BUF_LOSS) return copy_out(c, out, J.loss, need, s);
+  if (which == PDG_BUF_NN_FWD) return copy_out(c, out, J.nn_fwd, need, s);
+  if (which == PDG_BUF_NN_REV) return copy_out(c, out, J.nn_rev, need, s);
+  float* tmp = nullptr;
+  CU(c, cudaMallocAsync((void**)&tmp, need, s));
+  switch (which) {
+    case PDG_BUF_THETA: launch_unpack4(J.lev[level].theta, tmp, J.lev[level].n3, s); break;
+    case PDG_BUF_GRAD: launch_soa_to_aos(J.lev[level].g, tmp, J.lev[level].n3, s); break;
+    case PDG_BUF_PGRAD: launch_soa_to_aos(J.lev[level].tmp, tmp, J.lev[level].n3, s); break;
+    case PDG_BUF_Y: launch_unpack4(J.y, tmp, J.Q, s); break;
+    case PDG_BUF_POINT_GRAD: launch_unpack4(J.gy, tmp, J.Q, s); break;
+    case PDG_BUF_SOURCE: launch_unpack4(J.src4, tmp, J.N, s); break;
+  }
+  const pdg_status st = copy_out(c, out, tmp, need, s);
+  cudaFreeAsync(tmp, s);
+  return st;
+}
+
+pdg_status pdg_write_theta(pdg_ctx* c, int level, const float* theta, void* cuda_stream) {
+  if (!c || !theta) return PDG_ERR_INVALID;
+  if (level < 0 || level >= c->h.L) return c->fail(PDG_ERR_INVALID, "bad level");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const Level& lv = c->h.lev[level];
+  const float* src = theta;
+  float* tmp = nullptr;
+  const size_t bytes = sizeof(float) * 3 * (size_t)lv.n3;
+  if (!is_device_ptr(theta)) {
+    CU(c, cudaMallocAsync((void**)&tmp, bytes, s));
+    CU(c, cudaMemcpyAsync(tmp, theta, bytes, cudaMemcpyHostToDevice, s));
+    src = tmp;
+  }
+  launch_pack4(src, lv.theta, lv.n3, s);
+  CU(c, cudaMemsetAsync(lv.m, 0, 3 * sizeof(float) * lv.n3, s));
+  CU(c, cudaMemsetAsync(lv.v, 0, 3 * sizeof(float) * lv.n3, s));
+  if (tmp) {
+    CU(c, cudaFreeAsync(tmp, s));
+    CU(c, cudaStreamSynchronize(s));
+  }
+  return c->cuda(cudaGetLastError(), "write_theta");
+}
+
+// ------------------------------------------------------------------------------ batching
+
+pdg_status pdg_batch_create(int max_jobs, pdg_batch** out) {
+  if (!out || max_jobs < 1 || max_jobs > MAXJ) return PDG_ERR_INVALID;
+  pdg_batch* b = new pdg_batch();
+  b->max_jobs = max_jobs;
+  if (cudaMalloc(&b->dplan, sizeof(Plan)) != cudaSuccess || cudaMallocHost(&b->hplan, sizeof(Plan)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    pdg_batch_destroy(b);
+    return PDG_ERR_OOM;
+  }
+  std::memset(b->hplan, 0, sizeof(Plan));
+  *out = b;
+  return PDG_OK;
+}
+
+void pdg_batch_destroy(pdg_batch* b) {
+  if (!b) return;
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->dplan) cudaFree(b->dplan);
+  if (b->hplan) cudaFreeHost(b->hplan);
+  delete b;
+}
+
+pdg_status pdg_batch_set(pdg_batch* b, pdg_ctx* const* ctxs, int n_jobs) {
+  if (!b || n_jobs < 0 || n_jobs > b->max_jobs || (n_jobs && !ctxs)) return PDG_ERR_INVALID;
+  for (int i = 0; i < n_jobs; ++i) {
+    if (!ctxs[i]) return PDG_ERR_INVALID;
+    if (!ctxs[i]->in_frame) {
+      b->err = "batch member outside a frame";
+      return PDG_ERR_STATE;
+    }
+    for (int k = 0; k < i; ++k)
+      if (ctxs[k] == ctxs[i]) return PDG_ERR_INVALID;
+  }
+  b->members.assign(ctxs, ctxs + n_jobs);
+  b->n = n_jobs;
+  b->dirty = true;
+  return PDG_OK;
+}
+
+pdg_status pdg_batch_step(pdg_batch* b, int n_steps, void* cuda_stream) {
+  if (!b || n_steps < 0) return PDG_ERR_INVALID;
+  if (b->n == 0 || n_steps == 0) return PDG_OK;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int nmax = 1, sms = 1;
+  for (auto* c : b->members) {
+    if (!c->in_frame) {
+      b->err = "batch member outside a frame";
+      return PDG_ERR_STATE;
+    }
+    nmax = std::max(nmax, c->nmax);
+    sms = c->sms;
+  }
+  if (b->dirty) {
+    // publish the membership (stream-ordered; the pinned host copy is rewritten only after
+    // the previous upload completed)
+    if (cudaStreamSynchronize(s) != cudaSuccess) return PDG_ERR_CUDA;
+    std::memset(b->hplan, 0, sizeof(Plan));
+    b->hplan->n_jobs = b->n;
+    for (int i = 0; i < b->n; ++i) b->hplan->jobs[i] = b->members[i]->dJ;
+    if (cudaMemcpyAsync(b->dplan, b->hplan, sizeof(Plan), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return PDG_ERR_CUDA;
+    b->dirty = false;
+  }
+  if (!b->gexec || nmax > b->graph_nmax) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return PDG_ERR_CUDA;
+    const pdg_status st = capture_step(nullptr, b->dplan, nmax, b->cap, &b->gexec, &b->err, sms);
+    if (st != PDG_OK) return st;
+    b->graph_nmax = nmax;
+  }
+  for (int i = 0; i < n_steps; ++i)
+    if (cudaGraphLaunch(b->gexec, s) != cudaSuccess) return PDG_ERR_CUDA;
+  for (auto* c : b->members) c->steps_in_frame += n_steps;
+  return PDG_OK;
+}
+
+// ------------------------------------------------------------------------------ state
+
+namespace {
+struct StateHeader {
+  char magic[8];
+  int version, V, N, L, res[PDG_MAX_LEVELS];
+};
+}  // namespace
+
+size_t pdg_state_bytes(const pdg_ctx* c) {
+  if (!c) return 0;
+  size_t b = sizeof(StateHeader) + sizeof(float4) * (size_t)c->V + sizeof(float4) * (size_t)c->max_pts;
+  for (int l = 0; l < c->h.L; ++l) b += sizeof(float4) * (size_t)c->h.lev[l].n3;
+  return b;
+}
+
+pdg_status pdg_save_state(pdg_ctx* c, void* host_buf, size_t n, void* cuda_stream) {
+  if (!c || !host_buf) return PDG_ERR_INVALID;
+  if (c->in_frame) return c->fail(PDG_ERR_STATE, "save only between frames");
+  if (n < pdg_state_bytes(c)) return c->fail(PDG_ERR_INVALID, "state buffer too small");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  StateHeader hd{};
+  std::memcpy(hd.magic, "PDGSTAT", 8);
+  hd.version = 1;
+  hd.V = c->V;
+  hd.N = c->h.N;
+  hd.L = c->h.L;
+  for (int l = 0; l < c->h.L; ++l) hd.res[l] = c->h.lev[l].n;
+  char* p = (char*)host_buf;
+  std::memcpy(p, &hd, sizeof(hd));
+  p += sizeof(hd);
+  CU(c, cudaMemcpyAsync(p, c->h.verts4, sizeof(float4) * c->V, cudaMemcpyDeviceToHost, s));
+  p += sizeof(float4) * c->V;
+  CU(c, cudaMemcpyAsync(p, c->h.src4, sizeof(float4) * c->max_pts, cudaMemcpyDeviceToHost, s));
+  p += sizeof(float4) * c->max_pts;
+  for (int l = 0; l < c->h.L; ++l) {
+    CU(c, cudaMemcpyAsync(p, c->h.lev[l].theta, sizeof(float4) * c->h.lev[l].n3, cudaMemcpyDeviceToHost, s));
+    p += sizeof(float4) * c->h.lev[l].n3;
+  }
+  CU(c, cudaStreamSynchronize(s));
+  return PDG_OK;
+}
+
+pdg_status pdg_load_state(pdg_ctx* c, const void* host_buf, size_t n, void* cuda_stream) {
+  if (!c || !host_buf) return PDG_ERR_INVALID;
+  if (c->in_frame) return c->fail(PDG_ERR_STATE, "load only between frames");
+  if (n < pdg_state_bytes(c)) return c->fail(PDG_ERR_INVALID, "state buffer too small");
+  StateHeader hd;
+  std::memcpy(&hd, host_buf, sizeof(hd));
+  if (std::memcmp(hd.magic, "PDGSTAT", 8) != 0 || hd.version != 1 || hd.V != c->V || hd.L != c->h.L ||
+      hd.N < 1 || hd.N > c->max_pts)
+    return c->fail(PDG_ERR_INVALID, "state does not match this context");
+  for (int l = 0; l < c->h.L; ++l)
+    if (hd.res[l] != c->h.lev[l].n) return c->fail(PDG_ERR_INVALID, "state does not match this context");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const char* p = (const char*)host_buf + sizeof(hd);
+  CU(c, cudaMemcpyAsync(c->h.verts4, p, sizeof(float4) * c->V, cudaMemcpyHostToDevice, s));
+  p += sizeof(float4) * c->V;
+  CU(c, cudaMemcpyAsync(c->h.src4, p, sizeof(float4) * c->max_pts, cudaMemcpyHostToDevice, s));
+  p += sizeof(float4) * c->max_pts;
+  for (int l = 0; l < c->h.L; ++l) {
+    CU(c, cudaMemcpyAsync(c->h.lev[l].theta, p, sizeof(float4) * c->h.lev[l].n3, cudaMemcpyHostToDevice, s));
+    p += sizeof(float4) * c->h.lev[l].n3;
+  }
+  c->h.N = hd.N;
+  c->h.Q = c->V + hd.N;
+  TRY(upload_job(c, s));
+  CU(c, cudaStreamSynchronize(s));
+  return PDG_OK;
+}
+
+}  // extern "C"
