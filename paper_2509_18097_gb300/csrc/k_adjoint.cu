@@ -20,15 +20,11 @@ __device__ __forceinline__ int corners(const Job& J, const Level& lv, float px, 
     w[0] = 1.f;
     return 1;
   }
-  const float nm1 = (float)(n - 1);
-  float tx = (px - J.lo[0]) * (nm1 / (J.hi[0] - J.lo[0]));
-  float ty = (py - J.lo[1]) * (nm1 / (J.hi[1] - J.lo[1]));
-  float tz = (pz - J.lo[2]) * (nm1 / (J.hi[2] - J.lo[2]));
-  tx = fminf(fmaxf(tx, 0.f), nm1);
-  ty = fminf(fmaxf(ty, 0.f), nm1);
-  tz = fminf(fmaxf(tz, 0.f), nm1);
-  const int ix = min((int)floorf(tx), n - 2), iy = min((int)floorf(ty), n - 2), iz = min((int)floorf(tz), n - 2);
-  const float fx = tx - ix, fy = ty - iy, fz = tz - iz;
+  int ix, iy, iz;
+  float fx, fy, fz;
+  grid_coord(px, J.lo[0], lv.sc_hi[0], lv.sc_lo[0], n, ix, fx);
+  grid_coord(py, J.lo[1], lv.sc_hi[1], lv.sc_lo[1], n, iy, fy);
+  grid_coord(pz, J.lo[2], lv.sc_hi[2], lv.sc_lo[2], n, iz, fz);
   const int b = (iz * n + iy) * n + ix;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {

@@ -22,7 +22,6 @@ namespace pdg {
 struct Best {
   float d2;
   int idx;
-  float x, y, z;
 };
 
 __device__ __forceinline__ void consider(Best& b, const float4 p, float qx, float qy, float qz) {
@@ -31,9 +30,6 @@ __device__ __forceinline__ void consider(Best& b, const float4 p, float qx, floa
   if (d2 < b.d2 || (d2 == b.d2 && id < b.idx)) {
     b.d2 = d2;
     b.idx = id;
-    b.x = p.x;
-    b.y = p.y;
-    b.z = p.z;
   }
 }
 
@@ -59,35 +55,6 @@ __device__ __forceinline__ float outside_bound2(const CellGrid& g, float qx, flo
 }
 
 // ------------------------------------------------------------------------------ finalise
-
-// forward query: moving point a (Q index qid) -> nearest target point b
-__device__ __forceinline__ void finalize_fwd(const Job& J, int qid, float ax, float ay, float az, const Best& b) {
-  const float s = b.d2;
-  const float e = expf(-J.alpha * s);
-  const float phi = s * e;
-  const float dphi = J.stopgrad ? e : e * (1.f - J.alpha * s);
-  const bool mesh = qid < J.V;
-  const float coef = 2.f * dphi * (mesh ? J.w_mesh / (float)J.V : J.w_pts / (float)(J.Q - J.V));
-  J.loss_fwd[qid] = phi;
-  J.gfwd[qid] = make_float4(coef * (ax - b.x), coef * (ay - b.y), coef * (az - b.z), 0.f);
-  J.nn_fwd[qid] = b.idx;
-}
-
-// reverse query: target point bq (index bid) -> nearest moving point a of set `set`
-__device__ __forceinline__ void finalize_rev(const Job& J, int set, int bid, float bx, float by, float bz,
-                                             const Best& a) {
-  const float s = a.d2;
-  const float e = expf(-J.alpha * s);
-  const float phi = s * e;
-  const float dphi = J.stopgrad ? e : e * (1.f - J.alpha * s);
-  J.loss_rev[set * J.M + bid] = phi;
-  J.nn_rev[set * J.M + bid] = a.idx - (set ? J.V : 0);
-  const float c = 2.f * dphi;
-  unsigned long long* acc = reinterpret_cast<unsigned long long*>(J.acc + 3 * (size_t)a.idx);
-  atomicAdd(acc + 0, (unsigned long long)to_fx(c * (a.x - bx)));
-  atomicAdd(acc + 1, (unsigned long long)to_fx(c * (a.y - by)));
-  atomicAdd(acc + 2, (unsigned long long)to_fx(c * (a.z - bz)));
-}
 
 // Resolves a query item of a job into its point, grid and set.
 // items [0, Q): forward queries in moving-grid order; [Q, Q + 2M): reverse queries
@@ -117,6 +84,8 @@ __device__ __forceinline__ QueryRef resolve(const Job& J, int item) {
   return q;
 }
 
+// The loss term phi(s) = s e^{-alpha s} and the gradient 2 phi'(s) (a - b) of a matched
+// pair (Sec. 3.4); phi'(s) = e^{-alpha s}(1 - alpha s), or e^{-alpha s} with the stop-gradient.
 __device__ __forceinline__ void finalize(const Job& J, const QueryRef& q, const Best& b) {
   if (b.idx == 0x7fffffff || !(b.d2 < FLT_MAX)) {  // nothing found (non-finite coordinates)
     if (q.fwd) {
@@ -129,11 +98,52 @@ __device__ __forceinline__ void finalize(const Job& J, const QueryRef& q, const 
     }
     return;
   }
-  if (q.fwd) finalize_fwd(J, q.id, q.x, q.y, q.z, b);
-  else finalize_rev(J, q.set, q.id, q.x, q.y, q.z, b);
+  const float s = b.d2;
+  const float e = expf(-J.alpha * s);
+  const float phi = s * e;
+  const float dphi = J.stopgrad ? e : e * (1.f - J.alpha * s);
+  if (q.fwd) {  // moving point a = q -> target point b
+    const float4 t = J.tgt4[b.idx];
+    const bool mesh = q.id < J.V;
+    const float coef = 2.f * dphi * (mesh ? J.w_mesh / (float)J.V : J.w_pts / (float)(J.Q - J.V));
+    J.loss_fwd[q.id] = phi;
+    J.gfwd[q.id] = make_float4(coef * (q.x - t.x), coef * (q.y - t.y), coef * (q.z - t.z), 0.f);
+    J.nn_fwd[q.id] = b.idx;
+  } else {  // target point q -> moving point a of set q.set; the gradient goes to a
+    const float4 a = J.y[b.idx];
+    J.loss_rev[q.set * J.M + q.id] = phi;
+    J.nn_rev[q.set * J.M + q.id] = b.idx - (q.set ? J.V : 0);
+    const float c = 2.f * dphi;
+    unsigned long long* acc = reinterpret_cast<unsigned long long*>(J.acc + 3 * (size_t)b.idx);
+    atomicAdd(acc + 0, (unsigned long long)to_fx(c * (a.x - q.x)));
+    atomicAdd(acc + 1, (unsigned long long)to_fx(c * (a.y - q.y)));
+    atomicAdd(acc + 2, (unsigned long long)to_fx(c * (a.z - q.z)));
+  }
 }
 
-// ------------------------------------------------------------------------------ one-ring pass
+// ------------------------------------------------------------------------------ shells
+
+__device__ __forceinline__ void scan_range(const CellGrid& g, int s, int e, float qx, float qy, float qz, Best& b) {
+  for (int k = s; k < e; ++k) consider(b, __ldg(g.pts + k), qx, qy, qz);
+}
+
+// Candidates of row (dy, dz) of shell r around cell (cx, cy, cz): rows on the shell's
+// y/z boundary over the full x range [cx - r, cx + r], the others only at x = cx -/+ r.
+__device__ __forceinline__ void scan_shell_row(const CellGrid& g, int base, int G, int cx, int cy, int cz, int r,
+                                               int dy, int dz, float qx, float qy, float qz, Best& b) {
+  const int yy = cy + dy, zz = cz + dz;
+  if (yy < 0 || yy >= G || zz < 0 || zz >= G) return;
+  const int rk = base + row_key(yy, zz, g.bits);
+  if (max(abs(dy), abs(dz)) == r) {
+    const int x0 = max(cx - r, 0), x1 = min(cx + r, G - 1);
+    scan_range(g, __ldg(g.off + rk + x0), __ldg(g.off + rk + x1 + 1), qx, qy, qz, b);
+  } else {
+    if (cx - r >= 0) scan_range(g, __ldg(g.off + rk + cx - r), __ldg(g.off + rk + cx - r + 1), qx, qy, qz, b);
+    if (cx + r < G) scan_range(g, __ldg(g.off + rk + cx + r), __ldg(g.off + rk + cx + r + 1), qx, qy, qz, b);
+  }
+}
+
+// ------------------------------------------------------------------------------ thread pass
 
 __global__ void __launch_bounds__(256) k_nn(const Plan* __restrict__ P) {
   const int nj = P->n_jobs;
@@ -149,25 +159,34 @@ __global__ void __launch_bounds__(256) k_nn(const Plan* __restrict__ P) {
     const int cx = cell_coord(q.x, g.lo[0], g.inv_h[0], G);
     const int cy = cell_coord(q.y, g.lo[1], g.inv_h[1], G);
     const int cz = cell_coord(q.z, g.lo[2], g.inv_h[2], G);
-    const int x0 = max(cx - 1, 0), x1 = min(cx + 1, G - 1);
-    Best b{FLT_MAX, 0x7fffffff, 0.f, 0.f, 0.f};
-    for (int zz = max(cz - 1, 0); zz <= min(cz + 1, G - 1); ++zz) {
-      for (int yy = max(cy - 1, 0); yy <= min(cy + 1, G - 1); ++yy) {
-        const int rk = base + row_key(yy, zz, g.bits);
-        const int s = __ldg(g.off + rk + x0), e = __ldg(g.off + rk + x1 + 1);
-        for (int k = s; k < e; ++k) consider(b, __ldg(g.pts + k), q.x, q.y, q.z);
-      }
+    Best b{FLT_MAX, 0x7fffffff};
+    // ring 1: the 3x3x3 box as 9 x-rows
+    {
+      const int x0 = max(cx - 1, 0), x1 = min(cx + 1, G - 1);
+      for (int zz = max(cz - 1, 0); zz <= min(cz + 1, G - 1); ++zz)
+        for (int yy = max(cy - 1, 0); yy <= min(cy + 1, G - 1); ++yy) {
+          const int rk = base + row_key(yy, zz, g.bits);
+          scan_range(g, __ldg(g.off + rk + x0), __ldg(g.off + rk + x1 + 1), q.x, q.y, q.z, b);
+        }
     }
-    if (b.d2 < outside_bound2(g, q.x, q.y, q.z, cx, cy, cz, 1)) {
+    int r = 1;
+    bool done = b.d2 < outside_bound2(g, q.x, q.y, q.z, cx, cy, cz, 1);
+    while (!done && r < NN_RTHREAD) {
+      ++r;
+      for (int dz = -r; dz <= r; ++dz)
+        for (int dy = -r; dy <= r; ++dy) scan_shell_row(g, base, G, cx, cy, cz, r, dy, dz, q.x, q.y, q.z, b);
+      done = b.d2 < outside_bound2(g, q.x, q.y, q.z, cx, cy, cz, r);
+    }
+    if (done) {
       finalize(J, q, b);
     } else {
       const int slot = atomicAdd(J.hard_count, 1);
-      J.hard[slot] = item;
+      J.hard[slot] = make_int4(item, r, __float_as_int(b.d2), b.idx);
     }
   }
 }
 
-// ------------------------------------------------------------------------------ ring pass
+// ------------------------------------------------------------------------------ warp pass
 
 __device__ __forceinline__ unsigned long long pack(const Best& b) {
   return ((unsigned long long)__float_as_uint(b.d2) << 32) | (unsigned)b.idx;
@@ -181,19 +200,10 @@ __device__ __forceinline__ Best warp_min(const Best& b) {
     const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
     m = t < m ? t : m;
   }
-  const unsigned ball = __ballot_sync(0xffffffffu, pack(b) == m);
-  const int src = __ffs(ball) - 1;
   Best r;
   r.d2 = __uint_as_float((unsigned)(m >> 32));
   r.idx = (int)(unsigned)(m & 0xffffffffu);
-  r.x = __shfl_sync(0xffffffffu, b.x, src);
-  r.y = __shfl_sync(0xffffffffu, b.y, src);
-  r.z = __shfl_sync(0xffffffffu, b.z, src);
   return r;
-}
-
-__device__ __forceinline__ void scan_range(const CellGrid& g, int s, int e, const QueryRef& q, Best& b) {
-  for (int k = s; k < e; ++k) consider(b, __ldg(g.pts + k), q.x, q.y, q.z);
 }
 
 __global__ void __launch_bounds__(256) k_nn_hard(const Plan* __restrict__ P) {
@@ -218,34 +228,26 @@ __global__ void __launch_bounds__(256) k_nn_hard(const Plan* __restrict__ P) {
       if (hpre[mid] <= w) lo = mid; else hi = mid;
     }
     const Job& J = *P->jobs[lo];
-    const int item = J.hard[w - hpre[lo]];
-    const QueryRef q = resolve(J, item);
+    const int4 h = J.hard[w - hpre[lo]];
+    const QueryRef q = resolve(J, h.x);
     const CellGrid& g = q.fwd ? J.tgt : J.mov;
     const int G = 1 << g.bits;
     const int base = q.set * G * G * G;
     const int cx = cell_coord(q.x, g.lo[0], g.inv_h[0], G);
     const int cy = cell_coord(q.y, g.lo[1], g.inv_h[1], G);
     const int cz = cell_coord(q.z, g.lo[2], g.inv_h[2], G);
-    Best b{FLT_MAX, 0x7fffffff, 0.f, 0.f, 0.f};
+    // continue from the thread pass: its best is lane 0's starting candidate
+    Best b{FLT_MAX, 0x7fffffff};
+    if (lane == 0) {
+      b.d2 = __int_as_float(h.z);
+      b.idx = h.w;
+    }
     Best best = b;
     bool done = false;
-    for (int r = 0; r <= NN_RMAX && !done; ++r) {
-      // shell r: rows (dy, dz) in [-r, r]^2; rows on the shell's y/z boundary are scanned
-      // over the full x range, the others only at x = c -/+ r
+    for (int r = h.y + 1; r <= NN_RMAX && !done; ++r) {
       const int side = 2 * r + 1;
-      for (int ri = lane; ri < side * side; ri += 32) {
-        const int dy = ri % side - r, dz = ri / side - r;
-        const int yy = cy + dy, zz = cz + dz;
-        if (yy < 0 || yy >= G || zz < 0 || zz >= G) continue;
-        const int rk = base + row_key(yy, zz, g.bits);
-        if (max(abs(dy), abs(dz)) == r) {
-          const int x0 = max(cx - r, 0), x1 = min(cx + r, G - 1);
-          scan_range(g, __ldg(g.off + rk + x0), __ldg(g.off + rk + x1 + 1), q, b);
-        } else {
-          if (cx - r >= 0) scan_range(g, __ldg(g.off + rk + cx - r), __ldg(g.off + rk + cx - r + 1), q, b);
-          if (cx + r < G) scan_range(g, __ldg(g.off + rk + cx + r), __ldg(g.off + rk + cx + r + 1), q, b);
-        }
-      }
+      for (int ri = lane; ri < side * side; ri += 32)
+        scan_shell_row(g, base, G, cx, cy, cz, r, ri % side - r, ri / side - r, q.x, q.y, q.z, b);
       best = warp_min(b);
       done = best.d2 < outside_bound2(g, q.x, q.y, q.z, cx, cy, cz, r);
     }

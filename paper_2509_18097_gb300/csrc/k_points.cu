@@ -34,6 +34,7 @@ __global__ void k_plan(Plan* P, int bump) {
     cnt[ST_ADJ][j] = a;
     cnt[ST_TILE][j] = t;
     cnt[ST_JOB][j] = 1;
+    cnt[ST_LOSSCH][j] = (J->Q + 2 * J->M + J->E + LOSS_CHUNK - 1) / LOSS_CHUNK;
   }
   __syncthreads();
   if (threadIdx.x < NSTAGE) {
@@ -61,15 +62,11 @@ __device__ float3 eval_disp(const Job& J, float px, float py, float pz) {
       ux += t.x; uy += t.y; uz += t.z;
       continue;
     }
-    const float nm1 = (float)(n - 1);
-    float tx = (px - J.lo[0]) * (nm1 / (J.hi[0] - J.lo[0]));
-    float ty = (py - J.lo[1]) * (nm1 / (J.hi[1] - J.lo[1]));
-    float tz = (pz - J.lo[2]) * (nm1 / (J.hi[2] - J.lo[2]));
-    tx = fminf(fmaxf(tx, 0.f), nm1);
-    ty = fminf(fmaxf(ty, 0.f), nm1);
-    tz = fminf(fmaxf(tz, 0.f), nm1);
-    const int ix = min((int)floorf(tx), n - 2), iy = min((int)floorf(ty), n - 2), iz = min((int)floorf(tz), n - 2);
-    const float fx = tx - ix, fy = ty - iy, fz = tz - iz;
+    int ix, iy, iz;
+    float fx, fy, fz;
+    grid_coord(px, J.lo[0], lv.sc_hi[0], lv.sc_lo[0], n, ix, fx);
+    grid_coord(py, J.lo[1], lv.sc_hi[1], lv.sc_lo[1], n, iy, fy);
+    grid_coord(pz, J.lo[2], lv.sc_hi[2], lv.sc_lo[2], n, iz, fz);
     const float4* t0 = lv.theta + ((size_t)(iz * n + iy) * n + ix);
     const float4* t1 = t0 + (size_t)n * n;
     const float4 c000 = t0[0], c100 = t0[1], c010 = t0[n], c110 = t0[n + 1];
@@ -184,46 +181,77 @@ __global__ void k_assemble(const Plan* __restrict__ P) {
 
 // ------------------------------------------------------------------------------ loss
 
-// Fixed-order FP64 reduction of the per-query and per-edge terms into the job's loss
-// record: cd_mesh = mean_X phi + mean_P_t phi, cd_pts likewise, iso = mean |r|.
-__global__ void k_loss(const Plan* __restrict__ P) {
-  __shared__ double red[5][32];
-  const int nj = P->n_jobs;
-  for (int j = blockIdx.x; j < nj; j += gridDim.x) {
-    const Job& J = *P->jobs[j];
-    double s[5] = {0, 0, 0, 0, 0};
-    for (int i = threadIdx.x; i < J.Q; i += blockDim.x) s[i < J.V ? 0 : 1] += (double)J.loss_fwd[i];
-    for (int i = threadIdx.x; i < J.M; i += blockDim.x) {
-      s[2] += (double)J.loss_rev[i];
-      s[3] += (double)J.loss_rev[J.M + i];
-    }
-    for (int i = threadIdx.x; i < J.E; i += blockDim.x) s[4] += (double)J.loss_iso[i];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+// Loss record.  The per-query and per-edge terms of a job form one virtual array
+// [phi fwd (Q) | phi rev set 0 (M) | phi rev set 1 (M) | |r| (E)], cut into fixed chunks of
+// LOSS_CHUNK; each chunk is summed by one block in a fixed fp32 tree per term, and a second
+// kernel adds a job's chunk partials in order in FP64.  The partition depends only on the
+// job, so a job's loss is bitwise the same alone or in a batch.
+__device__ __forceinline__ float block_sum(float v, float* red) {
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
-      double v = s[k];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if (lane == 0) red[k][w] = v;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  float t = 0.f;
+  if (w == 0) {
+    t = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(256) k_loss_chunks(const Plan* __restrict__ P) {
+  __shared__ float red[32];
+  const int nj = P->n_jobs;
+  const int total = P->pre[ST_LOSSCH][nj];
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    const int j = find_job(P->pre[ST_LOSSCH], nj, it);
+    const Job& J = *P->jobs[j];
+    const int c = it - P->pre[ST_LOSSCH][j];
+    const int b0 = c * LOSS_CHUNK;
+    const int Q = J.Q, V = J.V, M = J.M;
+    const int n_all = Q + 2 * M + J.E;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
+    for (int i = b0 + threadIdx.x; i < min(b0 + LOSS_CHUNK, n_all); i += blockDim.x) {
+      if (i < V) s0 += J.loss_fwd[i];
+      else if (i < Q) s1 += J.loss_fwd[i];
+      else if (i < Q + M) s2 += J.loss_rev[i - Q];
+      else if (i < Q + 2 * M) s3 += J.loss_rev[i - Q];
+      else s4 += J.loss_iso[i - Q - 2 * M];
     }
-    __syncthreads();
+    const float t0 = block_sum(s0, red), t1 = block_sum(s1, red), t2 = block_sum(s2, red);
+    const float t3 = block_sum(s3, red), t4 = block_sum(s4, red);
     if (threadIdx.x == 0) {
-      double t[5];
-      for (int k = 0; k < 5; ++k) {
-        double v = 0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += red[k][q];
-        t[k] = v;
-      }
-      const double cdm = t[0] / J.V + t[2] / J.M;
-      const double cdp = t[1] / (J.Q - J.V) + t[3] / J.M;
-      const double iso = J.E > 0 ? t[4] / J.E : 0.0;
-      const double tot = (double)J.w_mesh * cdm + (double)J.w_pts * cdp + (double)J.w_iso * iso;
-      J.loss[0] = tot;
-      J.loss[1] = cdm;
-      J.loss[2] = cdp;
-      J.loss[3] = iso;
-      if (!isfinite(tot)) *J.status |= 1;
+      float* o = J.loss_part + 5 * c;
+      o[0] = t0; o[1] = t1; o[2] = t2; o[3] = t3; o[4] = t4;
     }
-    __syncthreads();
+  }
+}
+
+__global__ void k_loss_final(const Plan* __restrict__ P) {
+  const int nj = P->n_jobs;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nj; j += gridDim.x * blockDim.x) {
+    const Job& J = *P->jobs[j];
+    const int nch = (J.Q + 2 * J.M + J.E + LOSS_CHUNK - 1) / LOSS_CHUNK;
+    double t[5] = {0, 0, 0, 0, 0};
+    for (int c = 0; c < nch; ++c) {
+      t[0] += (double)J.loss_part[5 * c + 0];
+      t[1] += (double)J.loss_part[5 * c + 1];
+      t[2] += (double)J.loss_part[5 * c + 2];
+      t[3] += (double)J.loss_part[5 * c + 3];
+      t[4] += (double)J.loss_part[5 * c + 4];
+    }
+    const double cdm = t[0] / J.V + t[2] / J.M;
+    const double cdp = t[1] / (J.Q - J.V) + t[3] / J.M;
+    const double iso = J.E > 0 ? t[4] / J.E : 0.0;
+    const double tot = (double)J.w_mesh * cdm + (double)J.w_pts * cdp + (double)J.w_iso * iso;
+    J.loss[0] = tot;
+    J.loss[1] = cdm;
+    J.loss[2] = cdp;
+    J.loss[3] = iso;
+    if (!isfinite(tot)) *J.status |= 1;
   }
 }
 
@@ -307,7 +335,10 @@ void launch_interp(const Plan* P, int grid, cudaStream_t s) { k_interp<<<grid, 2
 void launch_mov_scatter(const Plan* P, int grid, cudaStream_t s) { k_mov_scatter<<<grid, 256, 0, s>>>(P); }
 void launch_iso_edges(const Plan* P, int grid, cudaStream_t s) { k_iso_edges<<<grid, 256, 0, s>>>(P); }
 void launch_assemble(const Plan* P, int grid, cudaStream_t s) { k_assemble<<<grid, 256, 0, s>>>(P); }
-void launch_loss(const Plan* P, int grid, cudaStream_t s) { k_loss<<<grid, 512, 0, s>>>(P); }
+void launch_loss(const Plan* P, int grid, cudaStream_t s) {
+  k_loss_chunks<<<grid, 256, 0, s>>>(P);
+  k_loss_final<<<1, 256, 0, s>>>(P);
+}
 
 void launch_pack4(const float* in, float4* out, int n, cudaStream_t s) {
   k_pack4<<<blocks_for(n, 256), 256, 0, s>>>(in, out, n);

@@ -17,6 +17,8 @@ constexpr int TILE_LINES = 32;       // lines per Sobolev tile (per channel)
 constexpr int SOB_WARPS = 8;
 constexpr int SOB_THREADS = SOB_WARPS * 32;
 constexpr int NN_RMAX = 8;           // ring radius after which a query is searched exhaustively
+constexpr int NN_RTHREAD = 2;        // rings searched by the one-thread-per-query pass
+constexpr int LOSS_CHUNK = 8192;     // elements per loss-reduction chunk
 constexpr double FX_SCALE = 1099511627776.0;  // 2^40: fixed-point scale of the reverse Chamfer sums
 
 // A uniform cell grid over the domain used by the exact nearest-neighbour search.
@@ -41,6 +43,7 @@ struct Level {
   int lg;      // log2(n)
   int n3;      // n^3
   int tiles;   // Sobolev tiles: ceil(n^2 / 32)
+  float sc_hi[3], sc_lo[3];  // (n - 1) / (hi - lo) per axis as a float pair (hi + lo)
   float lr;    // learning rate of the level (already x0.1 without preconditioning)
   float lam;   // lambda of the level
   float4* theta;  // [n3] values (x, y, z, 0)
@@ -92,7 +95,8 @@ struct Job {
   float4* verts4;          // [V] current deformed template X_{t-1}
   CellGrid tgt;            // target grid, one set, built per frame
   CellGrid mov;            // moving grid, two sets (template, source), rebuilt every step
-  int* hard;               // [Q + 2 max_pts] queries left by the one-ring search
+  int4* hard;              // [Q + 2 max_pts] queries left by the thread pass: (item, ring, d2 bits, idx)
+  float* loss_part;        // [loss chunks][5] partial sums
   int* hard_count;         // device scalar
   int* step;               // Adam step count k
   float* bias;             // [2] 1 / (1 - beta1^k), 1 / sqrt(1 - beta2^k) of the current step
@@ -100,7 +104,7 @@ struct Job {
   int* status;             // sticky error flags (1: non-finite loss)
 };
 
-enum Stage { ST_Q = 0, ST_NNQ, ST_E, ST_MOVCH, ST_ADJ, ST_TILE, ST_JOB, NSTAGE };
+enum Stage { ST_Q = 0, ST_NNQ, ST_E, ST_MOVCH, ST_ADJ, ST_TILE, ST_JOB, ST_LOSSCH, NSTAGE };
 
 struct Plan {
   int n_jobs;
@@ -152,6 +156,48 @@ __device__ __forceinline__ int cell_key(const CellGrid& g, float x, float y, flo
 __device__ __forceinline__ float sqdist(float ax, float ay, float az, float bx, float by, float bz) {
   const float dx = __fsub_rn(ax, bx), dy = __fsub_rn(ay, by), dz = __fsub_rn(az, bz);
   return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+
+// Grid coordinate of x in a level with n >= 2 vertices per axis (Eq. 1, vertex-aligned,
+// clamped, last cell closed): u = (x - lo) (n - 1) / (hi - lo), i0 = min(floor(u), n - 2),
+// f = u - i0.  x - lo is formed exactly (TwoSum) and multiplied by the scale held as a
+// float pair with an FMA two-product, so f carries ~1 ulp of error instead of
+// ulp(hi - lo) * (n - 1) (which would reach 1e-5 of a weight on 128^3 grids).
+__device__ __forceinline__ void grid_coord(float x, float lo, float s_hi, float s_lo, int n, int& i0, float& f) {
+  const float d = __fsub_rn(x, lo);
+  const float bv = __fsub_rn(d, x);
+  const float dl = __fadd_rn(__fsub_rn(x, __fsub_rn(d, bv)), __fsub_rn(-lo, bv));  // x - lo = d + dl exactly
+  const float p = __fmul_rn(d, s_hi);
+  const float e = __fmaf_rn(d, s_hi, -p);
+  const float ul = __fadd_rn(e, __fmaf_rn(d, s_lo, __fmul_rn(dl, s_hi)));       // u = p + ul
+  if (!(p > 0.f) && !(p == 0.f && ul > 0.f)) {  // u <= 0 (or NaN): clamp to vertex 0
+    i0 = 0;
+    f = 0.f;
+    return;
+  }
+  if (p > (float)(n - 1) || (p == (float)(n - 1) && ul >= 0.f)) {  // u >= n - 1: clamp to the last vertex
+    i0 = n - 2;
+    f = 1.f;
+    return;
+  }
+  float fl = floorf(p);
+  if (fl == p && ul < 0.f) fl -= 1.f;
+  int i = (int)fl;
+  float fr = __fadd_rn(__fsub_rn(p, fl), ul);
+  if (fr >= 1.f && i < n - 2) {
+    i += 1;
+    fr = __fsub_rn(fr, 1.f);
+  }
+  if (fr < 0.f && i > 0) {
+    i -= 1;
+    fr = __fadd_rn(fr, 1.f);
+  }
+  if (i > n - 2) {
+    i = n - 2;
+    fr = 1.f;
+  }
+  i0 = i;
+  f = fminf(fmaxf(fr, 0.f), 1.f);
 }
 
 __device__ __forceinline__ long long to_fx(float v) { return __float2ll_rn(v * 1099511627776.0f); }

@@ -119,7 +119,7 @@ struct Layout {
   size_t x, y, gfwd, gy, acc, loss_fwd, loss_rev, loss_iso, nn_fwd, nn_rev, edge_d, edges, e_prev, v2e_ptr, v2e;
   size_t src4, tgt4, verts4;
   size_t t_hist, t_off, t_keys, t_pts, t_csum, m_hist, m_off, m_keys, m_pts, m_csum;
-  size_t hard, hard_count, step, bias, loss, status;
+  size_t hard, hard_count, step, bias, loss, status, loss_part;
   int tbits, mbits;
 };
 
@@ -185,7 +185,8 @@ Layout make_layout(const pdg_config& c, int V, int E, int max_pts) {
   L.m_keys = a.take<int>(Q);
   L.m_pts = a.take<float4>(Q);
   L.m_csum = a.take<int>(2 * mG3 / SCAN_CHUNK + 2);
-  L.hard = a.take<int>(Q + 2 * (size_t)max_pts);
+  L.hard = a.take<int4>(Q + 2 * (size_t)max_pts);
+  L.loss_part = a.take<float>(5 * ((Q + 2 * (size_t)max_pts + std::max(E, 1)) / LOSS_CHUNK + 2));
   L.hard_count = a.take<int>(1);
   L.step = a.take<int>(1);
   L.bias = a.take<float>(2);
@@ -447,6 +448,11 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
     lv.tiles = (n * n + TILE_LINES - 1) / TILE_LINES;
     lv.lr = (float)(cfg->lr0 * std::pow((double)cfg->lr_growth, l) * (cfg->precondition ? 1.0 : 0.1));
     lv.lam = (float)(cfg->lambda0 * std::pow((double)cfg->lambda_growth, l));
+    for (int a = 0; a < 3; ++a) {
+      const double sc = (n - 1) / ((double)cfg->hi[a] - (double)cfg->lo[a]);
+      lv.sc_hi[a] = (float)sc;
+      lv.sc_lo[a] = (float)(sc - (double)lv.sc_hi[a]);
+    }
     lv.theta = (float4*)P(o.theta);
     lv.m = (float*)P(o.m);
     lv.v = (float*)P(o.v);
@@ -516,7 +522,8 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
   };
   grid_init(J.tgt, L.tbits, 1, L.t_hist, L.t_off, L.t_keys, L.t_pts, L.t_csum);
   grid_init(J.mov, L.mbits, 2, L.m_hist, L.m_off, L.m_keys, L.m_pts, L.m_csum);
-  J.hard = (int*)P(L.hard);
+  J.hard = (int4*)P(L.hard);
+  J.loss_part = (float*)P(L.loss_part);
   J.hard_count = (int*)P(L.hard_count);
   J.step = (int*)P(L.step);
   J.bias = (float*)P(L.bias);
