@@ -155,6 +155,13 @@ int pdg_profile_stages(void);
 const char* pdg_profile_stage_name(int i);
 pdg_status pdg_profile_step(pdg_ctx* ctx, int n_steps, double* stage_ms, void* cuda_stream);
 
+/* The grid Sobolev preconditioner of level `level` applied to a caller-given gradient:
+ * out = (I + lambda_l L_l)^{-2} g per channel (Sec. 3.2, Eq. 3; L_l the free-boundary
+ * 6-neighbour graph Laplacian of the level's vertex grid), with the same kernels as the
+ * step.  g, out: float [res^3][3], host or device.  Only between frames (the level's
+ * gradient buffers are used as scratch): PDG_ERR_STATE inside a frame.  Synchronises. */
+pdg_status pdg_precondition(pdg_ctx* ctx, int level, const float* g, float* out, void* cuda_stream);
+
 /* 1: keep the preconditioned gradient of each step readable as PDG_BUF_PGRAD. */
 pdg_status pdg_set_debug(pdg_ctx* ctx, int keep_pgrad);
 

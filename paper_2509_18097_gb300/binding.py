@@ -78,6 +78,7 @@ _SIGS = {
     "pdg_read": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]),
     "pdg_write_theta": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "pdg_set_debug": (C.c_int, [C.c_void_p, C.c_int]),
+    "pdg_precondition": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pdg_profile_stages": (C.c_int, []),
     "pdg_profile_stage_name": (C.c_char_p, [C.c_int]),
     "pdg_profile_step": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
@@ -247,6 +248,13 @@ def pdg_read(ctx, which: int, level: int, out, stream=None):
 def pdg_write_theta(ctx, level: int, theta, stream=None):
     a = _Arr(theta, np.float32, 3, "theta")
     _check(load().pdg_write_theta(ctx, int(level), a.ptr, _stream(stream)), ctx)
+
+
+def pdg_precondition(ctx, level: int, g, out, stream=None):
+    a = _Arr(g, np.float32, 3, "g")
+    o = _Arr(out, np.float32, 3, "out")
+    _check(load().pdg_precondition(ctx, int(level), a.ptr, o.ptr, _stream(stream)), ctx)
+    return out
 
 
 def pdg_set_debug(ctx, keep_pgrad: bool = True):

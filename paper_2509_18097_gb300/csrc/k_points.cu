@@ -26,13 +26,16 @@ __global__ void k_plan(Plan* P, int bump) {
     cnt[ST_NNQ][j] = J->Q + 2 * J->M;
     cnt[ST_E][j] = J->E;
     cnt[ST_MOVCH][j] = (2 * G * G * G + SCAN_CHUNK - 1) / SCAN_CHUNK;
-    int a = 0, t = 0;
+    int a = 0, t = 0, p3 = 0;
     for (int l = 0; l < J->L; ++l) {
       a += *J->lev[l].n_active;
-      t += J->lev[l].tiles;
+      if (J->lev[l].n > 128) t += J->lev[l].tiles;
+      else p3 += J->lev[l].n;
     }
     cnt[ST_ADJ][j] = a;
     cnt[ST_TILE][j] = t;
+    cnt[ST_PLANE][j] = 3 * p3;
+    cnt[ST_PLANE3][j] = p3;
     cnt[ST_JOB][j] = 1;
     cnt[ST_LOSSCH][j] = (J->Q + 2 * J->M + J->E + LOSS_CHUNK - 1) / LOSS_CHUNK;
   }
@@ -363,6 +366,16 @@ __global__ void k_soa_to_aos(const float* __restrict__ in, float* __restrict__ o
     out[3 * i + 1] = in[n3 + i];
     out[3 * i + 2] = in[2 * n3 + i];
   }
+}
+__global__ void k_aos_to_soa(const float* __restrict__ in, float* __restrict__ out, int n3) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += gridDim.x * blockDim.x) {
+    out[i] = in[3 * i];
+    out[n3 + i] = in[3 * i + 1];
+    out[2 * n3 + i] = in[3 * i + 2];
+  }
+}
+void launch_aos_to_soa(const float* in, float* out, int n3, cudaStream_t s) {
+  k_aos_to_soa<<<blocks_for(n3, 256), 256, 0, s>>>(in, out, n3);
 }
 __global__ void k_copy_int(const int* __restrict__ in, int* __restrict__ out, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = in[i];

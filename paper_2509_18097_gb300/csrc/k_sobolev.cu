@@ -1,4 +1,6 @@
-// Grid Sobolev preconditioning (Sec. 3.2, Eq. 3) fused with the Adam update (Sec. 3.6).
+// Grid Sobolev preconditioning (Sec. 3.2, Eq. 3) fused with the Adam update (Sec. 3.6) for
+// levels of 256^3 vertices, whose planes do not fit in shared memory (smaller levels use
+// the three-pass plane path of k_sobolev_plane.cu).
 //
 // L_l is the 6-neighbour graph Laplacian of the level's vertex grid with a free
 // boundary; it is the Kronecker sum of three path-graph Laplacians whose eigenvectors are
@@ -118,10 +120,12 @@ __global__ void __launch_bounds__(SOB_THREADS) k_sob(const Plan* __restrict__ P)
     if (PASS < 5 && !pre) continue;
     int t = it - P->pre[ST_TILE][j];
     int l = 0;
-    for (; l < J.L - 1; ++l) {
+    for (; l < J.L; ++l) {
+      if (J.lev[l].n <= 128) continue;
       if (t < J.lev[l].tiles) break;
       t -= J.lev[l].tiles;
     }
+    if (l >= J.L) continue;
     const Level& lv = J.lev[l];
     const int n = lv.n, lg = lv.lg, n3 = lv.n3, nl = n * n;
     const int r0 = t * TILE_LINES;
@@ -191,6 +195,10 @@ __global__ void __launch_bounds__(SOB_THREADS) k_sob(const Plan* __restrict__ P)
         float4 th = lv.theta[v];
         float* thc = &th.x;
 #pragma unroll
+        if (J.no_adam) {
+          for (int c = 0; c < 3; ++c) lv.tmp[(size_t)c * n3 + v] = tl[(c * n + x) * TS + tt];
+          continue;
+        }
         for (int c = 0; c < 3; ++c) {
           const float g = tl[(c * n + x) * TS + tt];
           if (J.keep_pgrad) lv.tmp[(size_t)c * n3 + v] = g;
@@ -217,7 +225,7 @@ void sobolev_configure() {
   cudaFuncSetAttribute(k_sob<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
-void launch_sobolev(const Plan* P, int grid, int nmax, cudaStream_t s) {
+void launch_sobolev_tiles(const Plan* P, int grid, int nmax, cudaStream_t s) {
   const int smem = sobolev_smem_bytes(nmax);
   k_sob<1><<<grid, SOB_THREADS, smem, s>>>(P);
   k_sob<2><<<grid, SOB_THREADS, smem, s>>>(P);

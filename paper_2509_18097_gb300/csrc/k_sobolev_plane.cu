@@ -1,0 +1,380 @@
+// Grid Sobolev preconditioning (Sec. 3.2, Eq. 3) fused with Adam (Sec. 3.6) for levels of
+// up to 128^3 vertices, in three passes over shared-memory planes:
+//   A  per (z-plane, channel): DCT-II along x, then along y           g   -> tmp
+//   B  per (y-slab, channel):  DCT-II along z, spectral scale
+//                              (1 + lambda (mu_kx + mu_ky + mu_kz))^{-2} / n^3, inverse along z
+//   C  per z-plane:            inverse along y and x, then Adam on theta, m, v, channel by
+//                              channel (theta is read-modified-written per channel; its plane
+//                              stays in L2 between the three channels)
+// Why the DCT: L_l, the free-boundary 6-neighbour Laplacian, is the Kronecker sum of three
+// path-graph Laplacians whose eigenvectors are the DCT-II basis vectors
+// cos(pi k (i + 1/2) / n) with eigenvalues mu_k = 4 sin^2(pi k / 2n), so the preconditioner
+// is diagonal in the 3-D DCT basis.
+//
+// A line transform handles two lines at once (packed as the real and imaginary parts of one
+// complex sequence after the even/odd reordering that turns a DCT-II into a DFT).  The
+// length-n complex FFT is a two-stage Cooley-Tukey split n = N1 x N2 done by a group of N1
+// threads: each thread runs an N2-point DFT in registers, applies the twiddles, the group
+// transposes through padded shared memory, and each thread runs N2/N1 DFTs of N1 points.
+#include "kernels.h"
+
+namespace pdg {
+
+// exp(-2 pi i k / 16), k < 8
+__device__ __forceinline__ float2 tw16(int k) {
+  switch (k) {
+    case 0: return make_float2(1.f, 0.f);
+    case 1: return make_float2(0.923879532511286756f, -0.382683432365089772f);
+    case 2: return make_float2(0.707106781186547524f, -0.707106781186547524f);
+    case 3: return make_float2(0.382683432365089772f, -0.923879532511286756f);
+    case 4: return make_float2(0.f, -1.f);
+    case 5: return make_float2(-0.382683432365089772f, -0.923879532511286756f);
+    case 6: return make_float2(-0.707106781186547524f, -0.707106781186547524f);
+    default: return make_float2(-0.923879532511286756f, -0.382683432365089772f);
+  }
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+template <int R>
+__host__ __device__ constexpr int bitrev(int k) {
+  int r = 0;
+  for (int b = 1; b < R; b <<= 1) r = (r << 1) | ((k & b) ? 1 : 0);
+  return r;
+}
+
+// In-register DFT of R <= 16 points (natural order in and out): radix-2 decimation in
+// frequency with constant twiddles, then the bit-reversal permutation.
+template <int R, bool INV>
+__device__ __forceinline__ void dft_reg(float2 (&a)[R]) {
+#pragma unroll
+  for (int span = R / 2; span >= 1; span >>= 1) {
+#pragma unroll
+    for (int start = 0; start < R; start += 2 * span) {
+#pragma unroll
+      for (int k = 0; k < span; ++k) {
+        const int i = start + k, j = i + span;
+        const float2 t = make_float2(a[i].x - a[j].x, a[i].y - a[j].y);
+        a[i] = make_float2(a[i].x + a[j].x, a[i].y + a[j].y);
+        if (k == 0) {
+          a[j] = t;
+        } else {
+          float2 w = tw16((k * 16) / (2 * span));
+          if (INV) w.y = -w.y;
+          a[j] = cmul(t, w);
+        }
+      }
+    }
+  }
+  float2 b[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) b[k] = a[bitrev<R>(k)];
+#pragma unroll
+  for (int k = 0; k < R; ++k) a[k] = b[k];
+}
+
+// Complex FFT of n = N1 * N2 points by a group of N1 threads (thread t).  In: reg[m] =
+// x[t + N1 m].  Out: reg[jj N1 + k1] = X[k2 + N2 k1] with k2 = t + N1 jj.  sc: the group's
+// scratch of N1 (N2 + 1) complex; twn[m] = exp(-2 pi i m / n).  All threads of the warp
+// must call it together (it synchronises the warp).
+template <int N1, int N2, bool INV>
+__device__ __forceinline__ void fft2(float2 (&reg)[N2], float2* sc, int t, const float2* __restrict__ twn) {
+  constexpr int n = N1 * N2;
+  dft_reg<N2, INV>(reg);
+  if (N1 > 1) {
+#pragma unroll
+    for (int k2 = 1; k2 < N2; ++k2) {
+      float2 w = __ldg(twn + ((t * k2) & (n - 1)));
+      if (INV) w.y = -w.y;
+      reg[k2] = cmul(reg[k2], w);
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) sc[t * (N2 + 1) + k2] = reg[k2];
+    __syncwarp();
+#pragma unroll
+    for (int jj = 0; jj < N2 / N1; ++jj) {
+      float2 r2[N1];
+#pragma unroll
+      for (int n1 = 0; n1 < N1; ++n1) r2[n1] = sc[n1 * (N2 + 1) + t + N1 * jj];
+      dft_reg<N1, INV>(r2);
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) reg[jj * N1 + k1] = r2[k1];
+    }
+    __syncwarp();
+  }
+}
+
+__device__ __forceinline__ int dsrc(int j, int n) { return j < (n >> 1) ? 2 * j : 2 * (n - 1 - j) + 1; }
+
+// Forward DCT-II (unnormalised) of lines A, B (element stride es) by a group; `act` false
+// groups take part in the synchronisation only.
+template <int N1, int N2>
+__device__ __forceinline__ void dct2_lines(float* A, float* B, int es, float2* sc, int t, bool act,
+                                          const float2* __restrict__ twn, const float2* __restrict__ tw4) {
+  constexpr int n = N1 * N2;
+  float2 reg[N2];
+#pragma unroll
+  for (int m = 0; m < N2; ++m) {
+    const int s = dsrc(t + N1 * m, n) * es;
+    reg[m] = act ? make_float2(A[s], B[s]) : make_float2(0.f, 0.f);
+  }
+  fft2<N1, N2, false>(reg, sc, t, twn);
+#pragma unroll
+  for (int jj = 0; jj < N2 / N1; ++jj)
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) sc[t + N1 * jj + N2 * k1] = reg[jj * N1 + k1];
+  __syncwarp();
+  if (act) {
+#pragma unroll
+    for (int m = 0; m < N2; ++m) {
+      const int k = t + N1 * m;
+      const float2 zk = sc[k];
+      const float2 zc = sc[(n - k) & (n - 1)];
+      // V_A = (Z_k + conj Z_{n-k}) / 2, V_B = (Z_k - conj Z_{n-k}) / 2i, X = Re(exp(-i pi k/2n) V)
+      const float2 va = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y - zc.y));
+      const float2 vb = make_float2(0.5f * (zk.y + zc.y), -0.5f * (zk.x - zc.x));
+      const float2 w = __ldg(tw4 + k);
+      A[k * es] = w.x * va.x - w.y * va.y;
+      B[k * es] = w.x * vb.x - w.y * vb.y;
+    }
+  }
+  __syncwarp();
+}
+
+// Inverse: A, B <- n C^{-1} A, n C^{-1} B (the 1/n per axis is folded into the scale).
+template <int N1, int N2>
+__device__ __forceinline__ void dct3_lines(float* A, float* B, int es, float2* sc, int t, bool act,
+                                          const float2* __restrict__ twn, const float2* __restrict__ tw4) {
+  constexpr int n = N1 * N2;
+  if (act) {
+#pragma unroll
+    for (int m = 0; m < N2; ++m) {
+      const int k = t + N1 * m;
+      const float a = A[k * es], an = k ? A[(n - k) * es] : 0.f;
+      const float b = B[k * es], bn = k ? B[(n - k) * es] : 0.f;
+      float2 w = __ldg(tw4 + k);
+      w.y = -w.y;  // exp(+i pi k / 2n);  V = w (X_k - i X_{n-k});  Z = V_A + i V_B
+      const float2 va = make_float2(w.x * a + w.y * an, w.y * a - w.x * an);
+      const float2 vb = make_float2(w.x * b + w.y * bn, w.y * b - w.x * bn);
+      sc[k] = make_float2(va.x - vb.y, va.y + vb.x);
+    }
+  }
+  __syncwarp();
+  float2 reg[N2];
+#pragma unroll
+  for (int m = 0; m < N2; ++m) reg[m] = sc[t + N1 * m];
+  __syncwarp();
+  fft2<N1, N2, true>(reg, sc, t, twn);
+  if (act) {
+#pragma unroll
+    for (int jj = 0; jj < N2 / N1; ++jj)
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) {
+        const int s = dsrc(t + N1 * jj + N2 * k1, n) * es;
+        A[s] = reg[jj * N1 + k1].x;
+        B[s] = reg[jj * N1 + k1].y;
+      }
+  }
+  __syncwarp();
+}
+
+constexpr int PL_THREADS = 256;
+
+__host__ __device__ constexpr int plane_n1(int n) { return n <= 16 ? 1 : (n == 32 ? 4 : (n == 64 ? 8 : (n == 128 ? 8 : 16))); }
+
+// shared memory of a plane pass for resolution n: plane [n][n + 1] floats + per-group scratch
+int plane_smem_bytes(int n) {
+  const int N1 = plane_n1(n), N2 = n / N1;
+  const int groups = PL_THREADS / N1;
+  const int sc = N1 > 1 ? N1 * (N2 + 1) : 1;
+  return n * (n + 1) * 4 + groups * (sc > n ? sc : n) * 8;
+}
+
+// Transforms the lines of a plane held in shared memory.  Line l starts at plane + l * ls
+// and has element stride es.  DIR: 0 forward, 1 inverse, 2 forward + scale + inverse (scale
+// uses the z-line's (kx, ky) = (line, y) and mu of the level).
+template <int N1, int N2, int DIR>
+__device__ void plane_lines(float* plane, int ls, int es, float2* scr, const Level& lv, int y_slab) {
+  constexpr int n = N1 * N2;
+  constexpr int groups = PL_THREADS / N1;
+  const int g = threadIdx.x / N1, t = threadIdx.x % N1;
+  float2* sc = scr + g * ((N1 > 1 && N1 * (N2 + 1) > n) ? N1 * (N2 + 1) : n);
+  for (int base = 0; base < n / 2; base += groups) {
+    const int p = base + g;
+    const bool act = p < n / 2;
+    const int pl = act ? p : 0;
+    float* A = plane + (2 * pl) * ls;
+    float* B = A + ls;
+    if (DIR == 0 || DIR == 2) dct2_lines<N1, N2>(A, B, es, sc, t, act, lv.tw, lv.tw4);
+    if (DIR == 2) {
+      if (act) {
+        const float inv_n3 = 1.f / (float)lv.n3;
+        const float my = __ldg(lv.mu + y_slab);
+        const float ma = __ldg(lv.mu + 2 * pl) + my, mb = __ldg(lv.mu + 2 * pl + 1) + my;
+#pragma unroll
+        for (int m = 0; m < N2; ++m) {
+          const int k = t + N1 * m;
+          const float me = __ldg(lv.mu + k);
+          const float ia = 1.f / (1.f + lv.lam * (ma + me));
+          const float ib = 1.f / (1.f + lv.lam * (mb + me));
+          A[k * es] *= ia * ia * inv_n3;
+          B[k * es] *= ib * ib * inv_n3;
+        }
+      }
+      __syncwarp();
+    }
+    if (DIR == 1 || DIR == 2) dct3_lines<N1, N2>(A, B, es, sc, t, act, lv.tw, lv.tw4);
+  }
+}
+
+template <int DIR>
+__device__ void plane_lines_n(int n, float* plane, int ls, int es, float2* scr, const Level& lv, int y_slab) {
+  switch (n) {
+    case 2: plane_lines<1, 2, DIR>(plane, ls, es, scr, lv, y_slab); break;
+    case 4: plane_lines<1, 4, DIR>(plane, ls, es, scr, lv, y_slab); break;
+    case 8: plane_lines<1, 8, DIR>(plane, ls, es, scr, lv, y_slab); break;
+    case 16: plane_lines<1, 16, DIR>(plane, ls, es, scr, lv, y_slab); break;
+    case 32: plane_lines<4, 8, DIR>(plane, ls, es, scr, lv, y_slab); break;
+    case 64: plane_lines<8, 8, DIR>(plane, ls, es, scr, lv, y_slab); break;
+    case 128: plane_lines<8, 16, DIR>(plane, ls, es, scr, lv, y_slab); break;
+    default: break;
+  }
+}
+
+// maps a plane item of a job to (level, index); `per` items per level (3n or n), only levels
+// with 1 <= n <= 128 take part
+__device__ __forceinline__ bool plane_item(const Job& J, int r, bool three, int& l, int& idx) {
+  for (l = 0; l < J.L; ++l) {
+    const int n = J.lev[l].n;
+    if (n > 128) continue;
+    const int c = three ? 3 * n : n;
+    if (r < c) {
+      idx = r;
+      return true;
+    }
+    r -= c;
+  }
+  return false;
+}
+
+// pass A (PASS 0) and pass B (PASS 1): per (plane, channel)
+template <int PASS>
+__global__ void __launch_bounds__(PL_THREADS, 2) k_sobp(const Plan* __restrict__ P) {
+  extern __shared__ float smem[];
+  const int nj = P->n_jobs;
+  const int total = P->pre[ST_PLANE][nj];
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    const int j = find_job(P->pre[ST_PLANE], nj, it);
+    const Job& J = *P->jobs[j];
+    if (!J.precondition) continue;
+    int l, idx;
+    if (!plane_item(J, it - P->pre[ST_PLANE][j], true, l, idx)) continue;
+    const Level& lv = J.lev[l];
+    const int n = lv.n, n3 = lv.n3, lg = lv.lg;
+    if (n == 1) {  // no transform: copy g to tmp (the scale is 1)
+      if (PASS == 0 && threadIdx.x == 0) lv.tmp[idx] = lv.g[idx];
+      continue;
+    }
+    const int c = idx >> lg, q = idx & (n - 1);  // channel, plane index (z for A, y for B)
+    const int S = n + 1;
+    float* plane = smem;
+    float2* scr = reinterpret_cast<float2*>(smem + ((n * S + 1) & ~1));
+    const float* src = (PASS == 0 ? lv.g : lv.tmp) + (size_t)c * n3;
+    // load: A: plane[y][x] = src[(q n + y) n + x];  B: plane[z][x] = src[(z n + q) n + x]
+    for (int e = threadIdx.x; e < n * n; e += PL_THREADS) {
+      const int r = e >> lg, x = e & (n - 1);
+      const size_t a = PASS == 0 ? ((size_t)(q << lg) + r) * n + x : ((size_t)(r << lg) + q) * n + x;
+      plane[r * S + x] = src[a];
+    }
+    __syncthreads();
+    if (PASS == 0) {
+      plane_lines_n<0>(n, plane, S, 1, scr, lv, 0);  // x-lines (rows)
+      __syncthreads();
+      plane_lines_n<0>(n, plane, 1, S, scr, lv, 0);  // y-lines (columns)
+    } else {
+      plane_lines_n<2>(n, plane, 1, S, scr, lv, q);  // z-lines (columns): forward, scale, inverse
+    }
+    __syncthreads();
+    float* dst = lv.tmp + (size_t)c * n3;
+    for (int e = threadIdx.x; e < n * n; e += PL_THREADS) {
+      const int r = e >> lg, x = e & (n - 1);
+      const size_t a = PASS == 0 ? ((size_t)(q << lg) + r) * n + x : ((size_t)(r << lg) + q) * n + x;
+      dst[a] = plane[r * S + x];
+    }
+    __syncthreads();
+  }
+}
+
+// pass C: per z-plane, channel by channel: inverse along y and x, then Adam
+__global__ void __launch_bounds__(PL_THREADS, 2) k_sobp_adam(const Plan* __restrict__ P) {
+  extern __shared__ float smem[];
+  const int nj = P->n_jobs;
+  const int total = P->pre[ST_PLANE3][nj];
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    const int j = find_job(P->pre[ST_PLANE3], nj, it);
+    const Job& J = *P->jobs[j];
+    int l, z;
+    if (!plane_item(J, it - P->pre[ST_PLANE3][j], false, l, z)) continue;
+    const Level& lv = J.lev[l];
+    const bool pre = J.precondition != 0;
+    const int n = lv.n, n3 = lv.n3, lg = lv.lg;
+    const int S = n + 1;
+    float* plane = smem;
+    float2* scr = reinterpret_cast<float2*>(smem + ((n * S + 1) & ~1));
+    const float b1 = J.beta1, b2 = J.beta2;
+    const float step = lv.lr * J.bias[0];
+    const float ib2 = J.bias[1];
+    const size_t base = (size_t)z * n * n;
+    for (int c = 0; c < 3; ++c) {
+      const float* src = (pre ? lv.tmp : lv.g) + (size_t)c * n3 + base;
+      for (int e = threadIdx.x; e < n * n; e += PL_THREADS) plane[(e >> lg) * S + (e & (n - 1))] = src[e];
+      __syncthreads();
+      if (pre && n > 1) {
+        plane_lines_n<1>(n, plane, 1, S, scr, lv, 0);  // y-lines
+        __syncthreads();
+        plane_lines_n<1>(n, plane, S, 1, scr, lv, 0);  // x-lines
+        __syncthreads();
+      }
+      float* mc = lv.m + (size_t)c * n3 + base;
+      float* vc = lv.v + (size_t)c * n3 + base;
+      float* th = reinterpret_cast<float*>(lv.theta + base) + c;
+      for (int e = threadIdx.x; e < n * n; e += PL_THREADS) {
+        const float g = plane[(e >> lg) * S + (e & (n - 1))];
+        if (J.keep_pgrad) lv.tmp[(size_t)c * n3 + base + e] = g;
+        if (J.no_adam) continue;
+        float m = mc[e], vv = vc[e];
+        m = b1 * m + (1.f - b1) * g;
+        vv = b2 * vv + (1.f - b2) * g * g;
+        mc[e] = m;
+        vc[e] = vv;
+        th[4 * (size_t)e] -= step * m / (sqrtf(vv) * ib2 + J.eps);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// largest shared memory a plane pass needs over the levels n <= nmax it may meet
+int plane_smem_max(int nmax) {
+  int m = 0;
+  for (int n = 2; n <= 128 && n <= (nmax < 2 ? 2 : nmax); n <<= 1) m = plane_smem_bytes(n) > m ? plane_smem_bytes(n) : m;
+  return m;
+}
+
+void sobolev_plane_configure() {
+  const int smem = plane_smem_max(128);
+  cudaFuncSetAttribute(k_sobp<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_sobp<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_sobp_adam, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+void launch_sobolev_plane(const Plan* P, int grid, int nmax, cudaStream_t s) {
+  const int smem = plane_smem_max(nmax);
+  k_sobp<0><<<grid, PL_THREADS, smem, s>>>(P);
+  k_sobp<1><<<grid, PL_THREADS, smem, s>>>(P);
+  k_sobp_adam<<<grid, PL_THREADS, smem, s>>>(P);
+}
+
+}  // namespace pdg

@@ -14,7 +14,8 @@ void launch_nn_hard(const Plan* P, int grid, cudaStream_t s);
 void launch_iso_edges(const Plan* P, int grid, cudaStream_t s);
 void launch_assemble(const Plan* P, int grid, cudaStream_t s);
 void launch_adjoint(const Plan* P, int grid, cudaStream_t s);
-void launch_sobolev(const Plan* P, int grid, int nmax, cudaStream_t s);
+void launch_sobolev_tiles(const Plan* P, int grid, int nmax, cudaStream_t s);
+void launch_sobolev_plane(const Plan* P, int grid, int nmax, cudaStream_t s);
 void launch_loss(const Plan* P, int grid, cudaStream_t s);
 
 // per frame / per call (one job)
@@ -39,6 +40,10 @@ void launch_scan_segments(const ScanSeg* hsegs, int nseg, ScanSeg* dsegs_scratch
 
 int sobolev_smem_bytes(int n);
 void sobolev_configure();
+void sobolev_plane_configure();
+int plane_smem_bytes(int n);
+int plane_smem_max(int nmax);
+void launch_aos_to_soa(const float* in, float* out, int n3, cudaStream_t s);
 
 // misc conversions
 void launch_soa_to_aos(const float* in, float* out, int n3, cudaStream_t s);

@@ -52,7 +52,7 @@ struct Level {
   float* g;       // [3][n3] dLoss/dTheta (zero at vertices no point touches)
   float* tmp;     // [3][n3] spectral work array (and preconditioned gradient in debug mode)
   float* mu;      // [n] eigenvalues 4 sin^2(pi k / 2n) of the 1-D path Laplacian
-  float2* tw;     // [n/2] FFT twiddles exp(-2 pi i k / n)
+  float2* tw;     // [n] FFT twiddles exp(-2 pi i k / n)
   float2* tw4;    // [n] DCT twiddles exp(-i pi k / 2n)
   // point -> vertex interpolation lists, built once per frame (x is fixed in a frame)
   int* cnt;       // [n3] per-vertex entry counts (zero between builds)
@@ -72,6 +72,7 @@ struct Job {
   float lo[3], hi[3];
   float alpha, w_mesh, w_pts, w_iso;
   int stopgrad, precondition, keep_pgrad;
+  int no_adam;             // 1: pass C stores the preconditioned gradient and skips Adam
   float beta1, beta2, eps;
   int V, N, M, E, Q;       // template verts, source pts, target pts, edges, V + N
   int max_pts;
@@ -104,7 +105,7 @@ struct Job {
   int* status;             // sticky error flags (1: non-finite loss)
 };
 
-enum Stage { ST_Q = 0, ST_NNQ, ST_E, ST_MOVCH, ST_ADJ, ST_TILE, ST_JOB, ST_LOSSCH, NSTAGE };
+enum Stage { ST_Q = 0, ST_NNQ, ST_E, ST_MOVCH, ST_ADJ, ST_TILE, ST_JOB, ST_LOSSCH, ST_PLANE, ST_PLANE3, NSTAGE };
 
 struct Plan {
   int n_jobs;

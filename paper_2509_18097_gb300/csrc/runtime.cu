@@ -67,6 +67,8 @@ struct pdg_ctx {
   Job h{};                 // host mirror of the device job struct
   Job* dJ = nullptr;       // device job struct (inside the arena)
   Plan* dplan = nullptr;   // device plan holding only this job
+  Job* op_job = nullptr;   // scratch job / plan for single-level operations
+  Plan* op_plan = nullptr;
   int* dflag = nullptr;
   float* stage = nullptr;  // [stage_pts][3] staging of host inputs
   int stage_pts = 0;
@@ -111,7 +113,7 @@ namespace {
 // sizes of every buffer of a context (used by pdg_query_bytes and pdg_create)
 struct Layout {
   size_t total = 0;
-  size_t job, plan, flag, stage;
+  size_t job, plan, flag, stage, op_job, op_plan;
   struct Lv {
     size_t theta, m, v, g, tmp, mu, tw, tw4, cnt, rowptr, flag, act_v, act_ptr, ent_p, ent_w, n_active, csum;
     int cap;
@@ -129,6 +131,8 @@ Layout make_layout(const pdg_config& c, int V, int E, int max_pts) {
   const int Q = V + max_pts;
   L.job = a.take<Job>(1);
   L.plan = a.take<Plan>(1);
+  L.op_job = a.take<Job>(1);
+  L.op_plan = a.take<Plan>(1);
   L.flag = a.take<int>(4);
   const int sp = std::max(V, max_pts);
   L.stage = a.take<float>(3 * (size_t)sp);
@@ -142,7 +146,7 @@ Layout make_layout(const pdg_config& c, int V, int E, int max_pts) {
     v.g = a.take<float>(3 * n3);
     v.tmp = a.take<float>(3 * n3);
     v.mu = a.take<float>(n);
-    v.tw = a.take<float2>(std::max<size_t>(n / 2, 1));
+    v.tw = a.take<float2>(n);
     v.tw4 = a.take<float2>(n);
     v.cnt = a.take<int>(n3);
     v.rowptr = a.take<int>(n3 + 1);
@@ -239,9 +243,9 @@ pdg_status upload_job(pdg_ctx* c, cudaStream_t s) {
 
 // The step as an explicit list of stages; the graph capture and the profiling path launch
 // exactly the same sequence.
-const char* const STAGE_NAMES[] = {"plan",    "interp",     "mov_scan",  "mov_scatter", "nn",
-                                   "nn_hard", "iso_edges",  "assemble",  "adjoint",     "sobolev",
-                                   "loss"};
+const char* const STAGE_NAMES[] = {"plan",     "interp",   "mov_scan", "mov_scatter",   "nn",
+                                   "nn_hard",  "iso_edges", "assemble", "adjoint",       "sobolev",
+                                   "sobolev_256", "loss"};
 constexpr int N_STAGES = sizeof(STAGE_NAMES) / sizeof(STAGE_NAMES[0]);
 
 void launch_stage(int i, const Plan* plan, int nmax, int sms, cudaStream_t s) {
@@ -258,8 +262,16 @@ void launch_stage(int i, const Plan* plan, int nmax, int sms, cudaStream_t s) {
     case 6: launch_iso_edges(plan, grid, s); break;
     case 7: launch_assemble(plan, grid, s); break;
     case 8: launch_adjoint(plan, grid, s); break;
-    case 9: launch_sobolev(plan, sms * tiles_per_sm, nmax, s); break;
-    case 10: launch_loss(plan, std::min(sms, MAXJ), s); break;
+    case 9: {
+      const int ps = plane_smem_max(nmax);
+      const int per_sm = std::max(1, std::min(8, (227 * 1024) / ps));
+      launch_sobolev_plane(plan, sms * per_sm, nmax, s);
+      break;
+    }
+    case 10:
+      if (nmax > 128) launch_sobolev_tiles(plan, sms * tiles_per_sm, nmax, s);
+      break;
+    case 11: launch_loss(plan, sms * 2, s); break;
   }
 }
 
@@ -372,6 +384,7 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
   if (cudaGetDevice(&c->dev) != cudaSuccess) return bail(PDG_ERR_CUDA);
   cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->dev);
   sobolev_configure();
+  sobolev_plane_configure();
 
   // edges to the host (validation + vertex -> edge lists)
   std::vector<int32_t> he(2 * (size_t)n_edges);
@@ -433,6 +446,8 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
   J.max_pts = max_pts;
   c->dJ = (Job*)P(L.job);
   c->dplan = (Plan*)P(L.plan);
+  c->op_job = (Job*)P(L.op_job);
+  c->op_plan = (Plan*)P(L.op_plan);
   c->dflag = (int*)P(L.flag);
   c->stage = (float*)P(L.stage);
   c->stage_pts = std::max(n_verts, max_pts);
@@ -472,14 +487,14 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
     lv.csum = (int*)P(o.csum);
     c->nmax = std::max(c->nmax, n);
     mu.resize(n);
-    tw.resize(std::max(n / 2, 1));
+    tw.resize(n);
     tw4.resize(n);
     for (int k = 0; k < n; ++k) {
       const double sk = std::sin(PI * k / (2.0 * n));
       mu[k] = (float)(4.0 * sk * sk);
       tw4[k] = make_float2((float)std::cos(PI * k / (2.0 * n)), (float)-std::sin(PI * k / (2.0 * n)));
     }
-    for (int k = 0; k < std::max(n / 2, 1); ++k)
+    for (int k = 0; k < n; ++k)
       tw[k] = make_float2((float)std::cos(2 * PI * k / n), (float)-std::sin(2 * PI * k / n));
     // pageable sources are staged before the call returns, so the vectors may be reused
     if (cudaMemcpyAsync(lv.mu, mu.data(), n * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -783,6 +798,42 @@ pdg_status pdg_write_theta(pdg_ctx* c, int level, const float* theta, void* cuda
     CU(c, cudaStreamSynchronize(s));
   }
   return c->cuda(cudaGetLastError(), "write_theta");
+}
+
+pdg_status pdg_precondition(pdg_ctx* c, int level, const float* g, float* out, void* cuda_stream) {
+  if (!c || !g || !out) return PDG_ERR_INVALID;
+  if (c->in_frame) return c->fail(PDG_ERR_STATE, "pdg_precondition only between frames");
+  if (level < 0 || level >= c->h.L) return c->fail(PDG_ERR_INVALID, "bad level");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const Level& lv = c->h.lev[level];
+  const size_t bytes = sizeof(float) * 3 * (size_t)lv.n3;
+  float* tmp = nullptr;
+  CU(c, cudaMallocAsync((void**)&tmp, bytes, s));
+  CU(c, cudaMemcpyAsync(tmp, g, bytes, is_device_ptr(g) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  launch_aos_to_soa(tmp, lv.g, lv.n3, s);
+  // a one-level copy of the job that stores the preconditioned gradient instead of Adam
+  Job oj = c->h;
+  oj.L = 1;
+  oj.lev[0] = lv;
+  oj.precondition = 1;
+  oj.keep_pgrad = 1;
+  oj.no_adam = 1;
+  Plan op;
+  std::memset(&op, 0, sizeof(op));
+  op.n_jobs = 1;
+  op.jobs[0] = c->op_job;
+  CU(c, cudaMemcpyAsync(c->op_job, &oj, sizeof(Job), cudaMemcpyHostToDevice, s));
+  CU(c, cudaMemcpyAsync(c->op_plan, &op, sizeof(Plan), cudaMemcpyHostToDevice, s));
+  launch_plan(c->op_plan, 0, s);
+  launch_stage(9, c->op_plan, lv.n, c->sms, s);
+  launch_stage(10, c->op_plan, lv.n, c->sms, s);
+  launch_soa_to_aos(lv.tmp, tmp, lv.n3, s);
+  CU(c, cudaGetLastError());
+  const pdg_status st = copy_out(c, out, tmp, bytes, s);
+  cudaFreeAsync(tmp, s);
+  CU(c, cudaMemsetAsync(lv.g, 0, bytes, s));
+  CU(c, cudaStreamSynchronize(s));
+  return st;
 }
 
 // ------------------------------------------------------------------------------ batching

@@ -53,6 +53,15 @@ def test_one_step_stagewise(case):
     print(case, info)
 
 
+def test_one_step_stagewise_headline():
+    """The headline workload at full size (50 412 vertices, 100k + 100k points,
+    16^3..128^3, grids N(0, 0.01^2)): every stage of one step against the oracle."""
+    w = synth.ellipsoid_pair(seed=0)
+    g = H.gpu_run(w, thetas=w.thetas)
+    info = H.stagewise(w, g, H.oracle_cfg(w))
+    print("headline", info)
+
+
 @pytest.mark.parametrize("variant", [dict(precondition=False), dict(robust_weight_stopgrad=True),
                                      dict(w_iso=0.0, w_chamfer_mesh=2.0, w_chamfer_pts=0.5)])
 def test_one_step_config_variants(variant):
