@@ -155,6 +155,14 @@ int pdg_profile_stages(void);
 const char* pdg_profile_stage_name(int i);
 pdg_status pdg_profile_step(pdg_ctx* ctx, int n_steps, double* stage_ms, void* cuda_stream);
 
+/* Evaluates the loss and its gradients at the current grids without changing them: the
+ * step's forward and backward kernels (evaluation, nearest neighbours and robust-Chamfer
+ * gradient, isometry gradient, adjoint into the grids), no preconditioner, no Adam, no
+ * step count.  Afterwards PDG_BUF_LOSS, PDG_BUF_GRAD (dLoss/dTheta per level),
+ * PDG_BUF_POINT_GRAD hold the results.  `loss` (host, may be NULL) receives total,
+ * cd_mesh, cd_pts, iso (the call then synchronises).  Inside a frame only. */
+pdg_status pdg_eval(pdg_ctx* ctx, double* loss, void* cuda_stream);
+
 /* The grid Sobolev preconditioner of level `level` applied to a caller-given gradient:
  * out = (I + lambda_l L_l)^{-2} g per channel (Sec. 3.2, Eq. 3; L_l the free-boundary
  * 6-neighbour graph Laplacian of the level's vertex grid), with the same kernels as the

@@ -79,6 +79,7 @@ _SIGS = {
     "pdg_write_theta": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "pdg_set_debug": (C.c_int, [C.c_void_p, C.c_int]),
     "pdg_precondition": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pdg_eval": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
     "pdg_profile_stages": (C.c_int, []),
     "pdg_profile_stage_name": (C.c_char_p, [C.c_int]),
     "pdg_profile_step": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
@@ -248,6 +249,13 @@ def pdg_read(ctx, which: int, level: int, out, stream=None):
 def pdg_write_theta(ctx, level: int, theta, stream=None):
     a = _Arr(theta, np.float32, 3, "theta")
     _check(load().pdg_write_theta(ctx, int(level), a.ptr, _stream(stream)), ctx)
+
+
+def pdg_eval(ctx, stream=None) -> np.ndarray:
+    """Loss (total, cd_mesh, cd_pts, iso) and gradients at the current grids, no update."""
+    out = (C.c_double * 4)()
+    _check(load().pdg_eval(ctx, out, _stream(stream)), ctx)
+    return np.array(out[:], np.float64)
 
 
 def pdg_precondition(ctx, level: int, g, out, stream=None):

@@ -3,8 +3,9 @@
 // The query points x are fixed for a whole frame, so the per-level point -> vertex lists
 // (point id, weight / L) are built once per frame by a counting sort keyed by vertex, and
 // compacted to the vertices that some point touches.  Each step then gathers every active
-// vertex's row.  A row is summed in 64-bit fixed point with a per-row scale chosen from the
-// row's largest term: integer addition is associative, so the result does not depend on
+// vertex's row.  A row is summed in 64-bit fixed point with a scale chosen from the step's
+// bound on |dLoss/dy| (taken in the assembly kernel): integer addition is associative, so
+// the result does not depend on
 // the (atomic, unordered) order in which the lists were filled, nor on how the row is split
 // across lanes.  No floating-point atomics are used.
 #include "kernels.h"
@@ -110,19 +111,30 @@ void launch_csr_build(Job* J, const Job& hJ, cudaStream_t s) {
 
 // ------------------------------------------------------------------------------ per step
 
-__device__ __forceinline__ float warp_max(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
 __device__ __forceinline__ long long warp_sum(long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// one warp per active vertex row; all levels of all jobs in one launch
+// Rows are taken 32 at a time per warp (all levels of all jobs in one launch).  Fine levels
+// (n >= 64, a few dozen entries per row) give each lane its own row; coarse levels (hundreds
+// to thousands of entries per row) sum each of the 32 rows with the whole warp.  Both sum
+// in the same 64-bit fixed point, so the result does not depend on the split.
+__device__ __forceinline__ void row_sum(const Level& lv, const float4* __restrict__ gy, int s, int e, int step,
+                                        float sc, long long& ax, long long& ay, long long& az) {
+  const int* __restrict__ ep = lv.ent_p;
+  const float* __restrict__ ew = lv.ent_w;
+#pragma unroll 4
+  for (int k = s; k < e; k += step) {
+    const float wt = __ldg(ew + k) * sc;  // exact: sc is a power of two
+    const float4 g = __ldg(gy + __ldg(ep + k));
+    ax += __float2ll_rn(wt * g.x);
+    ay += __float2ll_rn(wt * g.y);
+    az += __float2ll_rn(wt * g.z);
+  }
+}
+
 __global__ void __launch_bounds__(256) k_adjoint(const Plan* __restrict__ P) {
   const int nj = P->n_jobs;
   const int total = P->pre[ST_ADJ][nj];
@@ -131,51 +143,56 @@ __global__ void __launch_bounds__(256) k_adjoint(const Plan* __restrict__ P) {
   for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nwarps) {
     const int j = find_job(P->pre[ST_ADJ], nj, w);
     const Job& J = *P->jobs[j];
-    int r = w - P->pre[ST_ADJ][j];
-    int l = 0;
-    for (; l < J.L - 1; ++l) {
-      const int na = *J.lev[l].n_active;
-      if (r < na) break;
-      r -= na;
+    int gi = w - P->pre[ST_ADJ][j];
+    int l = 0, na = 0;
+    for (; l < J.L; ++l) {
+      na = *J.lev[l].n_active;
+      const int ng = (na + 31) >> 5;
+      if (gi < ng) break;
+      gi -= ng;
     }
+    if (l >= J.L) continue;
     const Level& lv = J.lev[l];
-    const int v = lv.act_v[r];
-    const int s = lv.act_ptr[r], e = lv.act_ptr[r + 1];
-    // pass 1: largest |w g| of the row
-    float mx = 0.f;
-    for (int k = s + lane; k < e; k += 32) {
-      const float wt = lv.ent_w[k];
-      const float4 g = J.gy[lv.ent_p[k]];
-      mx = fmaxf(mx, fmaxf(fabsf(wt * g.x), fmaxf(fabsf(wt * g.y), fabsf(wt * g.z))));
-    }
-    mx = warp_max(mx);
-    float ox = 0.f, oy = 0.f, oz = 0.f;
-    if (mx > 0.f && mx <= 3.0e38f) {
+    const int r0 = gi << 5;
+    // fixed-point scale from the step's bound on |dL/dy|: every term |w g| < 2^ex and a row
+    // has at most Q terms, so partial sums stay below 2^62
+    const float gm = __uint_as_float(*J.gmax);
+    const bool finite = gm <= 3.0e38f;
+    int sh = 0;
+    if (gm > 0.f && finite) {
       int ex;
-      frexpf(mx, &ex);                  // mx < 2^ex
-      const int lg = 32 - __clz(e - s);  // row length < 2^lg
-      const int sh = 62 - ex - lg;      // every partial sum stays below 2^62
-      long long ax = 0, ay = 0, az = 0;
-      for (int k = s + lane; k < e; k += 32) {
-        const float wt = lv.ent_w[k];
-        const float4 g = J.gy[lv.ent_p[k]];
-        ax += __float2ll_rn(ldexpf(wt * g.x, sh));
-        ay += __float2ll_rn(ldexpf(wt * g.y, sh));
-        az += __float2ll_rn(ldexpf(wt * g.z, sh));
-      }
-      ax = warp_sum(ax);
-      ay = warp_sum(ay);
-      az = warp_sum(az);
-      ox = ldexpf(__ll2float_rn(ax), -sh);
-      oy = ldexpf(__ll2float_rn(ay), -sh);
-      oz = ldexpf(__ll2float_rn(az), -sh);
-    } else if (!(mx <= 3.0e38f)) {
-      ox = oy = oz = __int_as_float(0x7fc00000);  // propagate a non-finite gradient
+      frexpf(gm, &ex);
+      sh = min(62 - ex - (32 - __clz(J.Q)), 126);
     }
-    if (lane == 0) {
-      lv.g[v] = ox;
-      lv.g[lv.n3 + v] = oy;
-      lv.g[2 * lv.n3 + v] = oz;
+    const float sc = exp2f((float)sh), isc = exp2f((float)-sh);
+    if (lv.n >= 64) {
+      const int r = r0 + lane;
+      if (r < na) {
+        long long ax = 0, ay = 0, az = 0;
+        if (gm > 0.f && finite) row_sum(lv, J.gy, __ldg(lv.act_ptr + r), __ldg(lv.act_ptr + r + 1), 1, sc, ax, ay, az);
+        const int v = __ldg(lv.act_v + r);
+        const float nan = __int_as_float(0x7fc00000);
+        lv.g[v] = finite ? __ll2float_rn(ax) * isc : nan;
+        lv.g[lv.n3 + v] = finite ? __ll2float_rn(ay) * isc : nan;
+        lv.g[2 * lv.n3 + v] = finite ? __ll2float_rn(az) * isc : nan;
+      }
+    } else {
+      const int rend = min(r0 + 32, na);
+      for (int r = r0; r < rend; ++r) {
+        long long ax = 0, ay = 0, az = 0;
+        if (gm > 0.f && finite)
+          row_sum(lv, J.gy, __ldg(lv.act_ptr + r) + lane, __ldg(lv.act_ptr + r + 1), 32, sc, ax, ay, az);
+        ax = warp_sum(ax);
+        ay = warp_sum(ay);
+        az = warp_sum(az);
+        if (lane == 0) {
+          const int v = __ldg(lv.act_v + r);
+          const float nan = __int_as_float(0x7fc00000);
+          lv.g[v] = finite ? __ll2float_rn(ax) * isc : nan;
+          lv.g[lv.n3 + v] = finite ? __ll2float_rn(ay) * isc : nan;
+          lv.g[2 * lv.n3 + v] = finite ? __ll2float_rn(az) * isc : nan;
+        }
+      }
     }
   }
 }

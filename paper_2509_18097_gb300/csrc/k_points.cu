@@ -7,17 +7,22 @@ namespace pdg {
 
 // ------------------------------------------------------------------------------ plan
 
-// Computes, on the device, the per-stage item prefixes over the jobs of a plan and (when
-// `bump`) advances each job's Adam step count and its bias-correction factors.  One block.
+// Computes, on the device, the per-stage item prefixes over the jobs of a plan.  bump = 1:
+// a new optimisation step (advances each job's Adam step count and its bias corrections
+// and clears the per-step counters); bump = 2: an evaluation (clears the counters only).
+// One block.
 __global__ void k_plan(Plan* P, int bump) {
   __shared__ int cnt[NSTAGE][MAXJ];
   const int nj = P->n_jobs;
   for (int j = threadIdx.x; j < nj; j += blockDim.x) {
     Job* J = P->jobs[j];
     if (bump) {
+      *J->hard_count = 0;
+      *J->gmax = 0u;
+    }
+    if (bump == 1) {
       int k = *J->step + 1;
       *J->step = k;
-      *J->hard_count = 0;
       J->bias[0] = (float)(1.0 / (1.0 - pow((double)J->beta1, (double)k)));
       J->bias[1] = (float)(1.0 / sqrt(1.0 - pow((double)J->beta2, (double)k)));
     }
@@ -28,14 +33,14 @@ __global__ void k_plan(Plan* P, int bump) {
     cnt[ST_MOVCH][j] = (2 * G * G * G + SCAN_CHUNK - 1) / SCAN_CHUNK;
     int a = 0, t = 0, p3 = 0;
     for (int l = 0; l < J->L; ++l) {
-      a += *J->lev[l].n_active;
+      a += (*J->lev[l].n_active + 31) >> 5;  // adjoint: groups of 32 rows
       if (J->lev[l].n > 128) t += J->lev[l].tiles;
       else p3 += J->lev[l].n;
     }
     cnt[ST_ADJ][j] = a;
     cnt[ST_TILE][j] = t;
     cnt[ST_PLANE][j] = 3 * p3;
-    cnt[ST_PLANE3][j] = p3;
+    cnt[ST_PLANE3][j] = p3;  // (kept for the stage table; pass C uses ST_PLANE)
     cnt[ST_JOB][j] = 1;
     cnt[ST_LOSSCH][j] = (J->Q + 2 * J->M + J->E + LOSS_CHUNK - 1) / LOSS_CHUNK;
   }
@@ -179,6 +184,13 @@ __global__ void k_assemble(const Plan* __restrict__ P) {
       g.z += J.w_iso * iz;
     }
     J.gy[p] = g;
+    // running bound on |dL/dy| of the job (order-independent max, one atomic per job per warp)
+    unsigned bits = __float_as_uint(fmaxf(fabsf(g.x), fmaxf(fabsf(g.y), fabsf(g.z))));
+    if (!(fmaxf(fabsf(g.x), fmaxf(fabsf(g.y), fabsf(g.z))) <= 3.0e38f)) bits = 0x7f800000u;
+    const unsigned act = __activemask();
+    const unsigned same = __match_any_sync(act, j);
+    const unsigned m = __reduce_max_sync(same, bits);
+    if ((threadIdx.x & 31) == __ffs(same) - 1) atomicMax(J.gmax, m);
   }
 }
 
@@ -233,28 +245,32 @@ __global__ void __launch_bounds__(256) k_loss_chunks(const Plan* __restrict__ P)
   }
 }
 
-__global__ void k_loss_final(const Plan* __restrict__ P) {
+__global__ void __launch_bounds__(256) k_loss_final(const Plan* __restrict__ P) {
+  __shared__ float red[32];
   const int nj = P->n_jobs;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nj; j += gridDim.x * blockDim.x) {
+  for (int j = blockIdx.x; j < nj; j += gridDim.x) {
     const Job& J = *P->jobs[j];
     const int nch = (J.Q + 2 * J.M + J.E + LOSS_CHUNK - 1) / LOSS_CHUNK;
-    double t[5] = {0, 0, 0, 0, 0};
-    for (int c = 0; c < nch; ++c) {
-      t[0] += (double)J.loss_part[5 * c + 0];
-      t[1] += (double)J.loss_part[5 * c + 1];
-      t[2] += (double)J.loss_part[5 * c + 2];
-      t[3] += (double)J.loss_part[5 * c + 3];
-      t[4] += (double)J.loss_part[5 * c + 4];
+    float s[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int c = threadIdx.x; c < nch; c += blockDim.x) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) s[k] += J.loss_part[5 * c + k];
     }
-    const double cdm = t[0] / J.V + t[2] / J.M;
-    const double cdp = t[1] / (J.Q - J.V) + t[3] / J.M;
-    const double iso = J.E > 0 ? t[4] / J.E : 0.0;
-    const double tot = (double)J.w_mesh * cdm + (double)J.w_pts * cdp + (double)J.w_iso * iso;
-    J.loss[0] = tot;
-    J.loss[1] = cdm;
-    J.loss[2] = cdp;
-    J.loss[3] = iso;
-    if (!isfinite(tot)) *J.status |= 1;
+    double t[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) t[k] = (double)block_sum(s[k], red);  // all terms are >= 0
+    if (threadIdx.x == 0) {
+      const double cdm = t[0] / J.V + t[2] / J.M;
+      const double cdp = t[1] / (J.Q - J.V) + t[3] / J.M;
+      const double iso = J.E > 0 ? t[4] / J.E : 0.0;
+      const double tot = (double)J.w_mesh * cdm + (double)J.w_pts * cdp + (double)J.w_iso * iso;
+      J.loss[0] = tot;
+      J.loss[1] = cdm;
+      J.loss[2] = cdp;
+      J.loss[3] = iso;
+      if (!isfinite(tot)) *J.status |= 1;
+    }
+    __syncthreads();
   }
 }
 
@@ -340,7 +356,7 @@ void launch_iso_edges(const Plan* P, int grid, cudaStream_t s) { k_iso_edges<<<g
 void launch_assemble(const Plan* P, int grid, cudaStream_t s) { k_assemble<<<grid, 256, 0, s>>>(P); }
 void launch_loss(const Plan* P, int grid, cudaStream_t s) {
   k_loss_chunks<<<grid, 256, 0, s>>>(P);
-  k_loss_final<<<1, 256, 0, s>>>(P);
+  k_loss_final<<<MAXJ, 256, 0, s>>>(P);
 }
 
 void launch_pack4(const float* in, float4* out, int n, cudaStream_t s) {

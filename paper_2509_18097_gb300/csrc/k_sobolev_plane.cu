@@ -243,6 +243,42 @@ __device__ void plane_lines_n(int n, float* plane, int ls, int es, float2* scr, 
   }
 }
 
+// Copies an n x n plane between global rows (row r at src + r * rstride, n contiguous
+// floats) and the padded shared plane (row stride n + 1), 16 bytes per access for n >= 4,
+// with several loads in flight per thread.
+__device__ __forceinline__ void plane_load(float* __restrict__ plane, const float* __restrict__ src, int n, int lg,
+                                           size_t rstride) {
+  const int S = n + 1;
+  if (n >= 4) {
+    const int nq = (n * n) >> 2;
+#pragma unroll 4
+    for (int i = threadIdx.x; i < nq; i += PL_THREADS) {
+      const int e = i << 2, r = e >> lg, x = e & (n - 1);
+      const float4 q = __ldg(reinterpret_cast<const float4*>(src + r * rstride + x));
+      float* d = plane + r * S + x;
+      d[0] = q.x; d[1] = q.y; d[2] = q.z; d[3] = q.w;
+    }
+  } else {
+    for (int e = threadIdx.x; e < n * n; e += PL_THREADS) plane[(e >> lg) * S + (e & (n - 1))] = src[(e >> lg) * rstride + (e & (n - 1))];
+  }
+}
+
+__device__ __forceinline__ void plane_store(float* __restrict__ dst, const float* __restrict__ plane, int n, int lg,
+                                            size_t rstride) {
+  const int S = n + 1;
+  if (n >= 4) {
+    const int nq = (n * n) >> 2;
+#pragma unroll 4
+    for (int i = threadIdx.x; i < nq; i += PL_THREADS) {
+      const int e = i << 2, r = e >> lg, x = e & (n - 1);
+      const float* s = plane + r * S + x;
+      *reinterpret_cast<float4*>(dst + r * rstride + x) = make_float4(s[0], s[1], s[2], s[3]);
+    }
+  } else {
+    for (int e = threadIdx.x; e < n * n; e += PL_THREADS) dst[(e >> lg) * rstride + (e & (n - 1))] = plane[(e >> lg) * S + (e & (n - 1))];
+  }
+}
+
 // maps a plane item of a job to (level, index); `per` items per level (3n or n), only levels
 // with 1 <= n <= 128 take part
 __device__ __forceinline__ bool plane_item(const Job& J, int r, bool three, int& l, int& idx) {
@@ -281,13 +317,10 @@ __global__ void __launch_bounds__(PL_THREADS, 2) k_sobp(const Plan* __restrict__
     const int S = n + 1;
     float* plane = smem;
     float2* scr = reinterpret_cast<float2*>(smem + ((n * S + 1) & ~1));
-    const float* src = (PASS == 0 ? lv.g : lv.tmp) + (size_t)c * n3;
-    // load: A: plane[y][x] = src[(q n + y) n + x];  B: plane[z][x] = src[(z n + q) n + x]
-    for (int e = threadIdx.x; e < n * n; e += PL_THREADS) {
-      const int r = e >> lg, x = e & (n - 1);
-      const size_t a = PASS == 0 ? ((size_t)(q << lg) + r) * n + x : ((size_t)(r << lg) + q) * n + x;
-      plane[r * S + x] = src[a];
-    }
+    // A: rows y of z-plane q (row stride n);  B: rows z of the y-slab q (row stride n^2)
+    const size_t off = (size_t)c * n3 + (PASS == 0 ? (size_t)q * n * n : (size_t)q * n);
+    const size_t rstride = PASS == 0 ? (size_t)n : (size_t)n * n;
+    plane_load(plane, (PASS == 0 ? lv.g : lv.tmp) + off, n, lg, rstride);
     __syncthreads();
     if (PASS == 0) {
       plane_lines_n<0>(n, plane, S, 1, scr, lv, 0);  // x-lines (rows)
@@ -297,62 +330,85 @@ __global__ void __launch_bounds__(PL_THREADS, 2) k_sobp(const Plan* __restrict__
       plane_lines_n<2>(n, plane, 1, S, scr, lv, q);  // z-lines (columns): forward, scale, inverse
     }
     __syncthreads();
-    float* dst = lv.tmp + (size_t)c * n3;
-    for (int e = threadIdx.x; e < n * n; e += PL_THREADS) {
-      const int r = e >> lg, x = e & (n - 1);
-      const size_t a = PASS == 0 ? ((size_t)(q << lg) + r) * n + x : ((size_t)(r << lg) + q) * n + x;
-      dst[a] = plane[r * S + x];
-    }
+    plane_store(lv.tmp + off, plane, n, lg, rstride);
     __syncthreads();
   }
 }
 
-// pass C: per z-plane, channel by channel: inverse along y and x, then Adam
+// pass C: per (z-plane, channel): inverse along y and x, then Adam on that channel (theta
+// keeps x, y, z in one float4; each channel's item writes only its own component)
 __global__ void __launch_bounds__(PL_THREADS, 2) k_sobp_adam(const Plan* __restrict__ P) {
   extern __shared__ float smem[];
   const int nj = P->n_jobs;
-  const int total = P->pre[ST_PLANE3][nj];
+  const int total = P->pre[ST_PLANE][nj];
   for (int it = blockIdx.x; it < total; it += gridDim.x) {
-    const int j = find_job(P->pre[ST_PLANE3], nj, it);
+    const int j = find_job(P->pre[ST_PLANE], nj, it);
     const Job& J = *P->jobs[j];
-    int l, z;
-    if (!plane_item(J, it - P->pre[ST_PLANE3][j], false, l, z)) continue;
+    int l, idx;
+    if (!plane_item(J, it - P->pre[ST_PLANE][j], true, l, idx)) continue;
     const Level& lv = J.lev[l];
     const bool pre = J.precondition != 0;
     const int n = lv.n, n3 = lv.n3, lg = lv.lg;
+    const int c = idx >> lg, z = idx & (n - 1);
     const int S = n + 1;
     float* plane = smem;
     float2* scr = reinterpret_cast<float2*>(smem + ((n * S + 1) & ~1));
-    const float b1 = J.beta1, b2 = J.beta2;
+    const size_t base = (size_t)z * n * n;
+    plane_load(plane, (pre ? lv.tmp : lv.g) + (size_t)c * n3 + base, n, lg, n);
+    __syncthreads();
+    if (pre && n > 1) {
+      plane_lines_n<1>(n, plane, 1, S, scr, lv, 0);  // y-lines
+      __syncthreads();
+      plane_lines_n<1>(n, plane, S, 1, scr, lv, 0);  // x-lines
+      __syncthreads();
+    }
+    float* __restrict__ mc = lv.m + (size_t)c * n3 + base;
+    float* __restrict__ vc = lv.v + (size_t)c * n3 + base;
+    float* __restrict__ th = reinterpret_cast<float*>(lv.theta + base) + c;
+    float* __restrict__ pg = lv.tmp + (size_t)c * n3 + base;
+    const float b1 = J.beta1, b2 = J.beta2, eps = J.eps;
     const float step = lv.lr * J.bias[0];
     const float ib2 = J.bias[1];
-    const size_t base = (size_t)z * n * n;
-    for (int c = 0; c < 3; ++c) {
-      const float* src = (pre ? lv.tmp : lv.g) + (size_t)c * n3 + base;
-      for (int e = threadIdx.x; e < n * n; e += PL_THREADS) plane[(e >> lg) * S + (e & (n - 1))] = src[e];
-      __syncthreads();
-      if (pre && n > 1) {
-        plane_lines_n<1>(n, plane, 1, S, scr, lv, 0);  // y-lines
-        __syncthreads();
-        plane_lines_n<1>(n, plane, S, 1, scr, lv, 0);  // x-lines
-        __syncthreads();
+    const bool keep = J.keep_pgrad != 0, adam = J.no_adam == 0;
+    if (n >= 4) {
+      const int nq = (n * n) >> 2;
+#pragma unroll 2
+      for (int i = threadIdx.x; i < nq; i += PL_THREADS) {
+        const int e = i << 2;
+        const float* sp = plane + (e >> lg) * S + (e & (n - 1));
+        const float g[4] = {sp[0], sp[1], sp[2], sp[3]};
+        if (keep) *reinterpret_cast<float4*>(pg + e) = make_float4(g[0], g[1], g[2], g[3]);
+        if (!adam) continue;
+        float4 m4 = *reinterpret_cast<const float4*>(mc + e);
+        float4 v4 = *reinterpret_cast<const float4*>(vc + e);
+        float t[4] = {th[4 * (size_t)e], th[4 * (size_t)e + 4], th[4 * (size_t)e + 8], th[4 * (size_t)e + 12]};
+        float* mm = &m4.x;
+        float* vv = &v4.x;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          mm[k] = b1 * mm[k] + (1.f - b1) * g[k];
+          vv[k] = b2 * vv[k] + (1.f - b2) * g[k] * g[k];
+          t[k] -= step * mm[k] / (sqrtf(vv[k]) * ib2 + eps);
+        }
+        *reinterpret_cast<float4*>(mc + e) = m4;
+        *reinterpret_cast<float4*>(vc + e) = v4;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) th[4 * (size_t)(e + k)] = t[k];
       }
-      float* mc = lv.m + (size_t)c * n3 + base;
-      float* vc = lv.v + (size_t)c * n3 + base;
-      float* th = reinterpret_cast<float*>(lv.theta + base) + c;
+    } else {
       for (int e = threadIdx.x; e < n * n; e += PL_THREADS) {
         const float g = plane[(e >> lg) * S + (e & (n - 1))];
-        if (J.keep_pgrad) lv.tmp[(size_t)c * n3 + base + e] = g;
-        if (J.no_adam) continue;
+        if (keep) pg[e] = g;
+        if (!adam) continue;
         float m = mc[e], vv = vc[e];
         m = b1 * m + (1.f - b1) * g;
         vv = b2 * vv + (1.f - b2) * g * g;
         mc[e] = m;
         vc[e] = vv;
-        th[4 * (size_t)e] -= step * m / (sqrtf(vv) * ib2 + J.eps);
+        th[4 * (size_t)e] -= step * m / (sqrtf(vv) * ib2 + eps);
       }
-      __syncthreads();
     }
+    __syncthreads();
   }
 }
 

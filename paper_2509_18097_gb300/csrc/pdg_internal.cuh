@@ -18,7 +18,7 @@ constexpr int SOB_WARPS = 8;
 constexpr int SOB_THREADS = SOB_WARPS * 32;
 constexpr int NN_RMAX = 8;           // ring radius after which a query is searched exhaustively
 constexpr int NN_RTHREAD = 2;        // rings searched by the one-thread-per-query pass
-constexpr int LOSS_CHUNK = 8192;     // elements per loss-reduction chunk
+constexpr int LOSS_CHUNK = 2048;     // elements per loss-reduction chunk
 constexpr double FX_SCALE = 1099511627776.0;  // 2^40: fixed-point scale of the reverse Chamfer sums
 
 // A uniform cell grid over the domain used by the exact nearest-neighbour search.
@@ -98,6 +98,7 @@ struct Job {
   CellGrid mov;            // moving grid, two sets (template, source), rebuilt every step
   int4* hard;              // [Q + 2 max_pts] queries left by the thread pass: (item, ring, d2 bits, idx)
   float* loss_part;        // [loss chunks][5] partial sums
+  unsigned* gmax;          // max |dLoss/dy| component of the step (float bits; sets the adjoint's fixed-point scale)
   int* hard_count;         // device scalar
   int* step;               // Adam step count k
   float* bias;             // [2] 1 / (1 - beta1^k), 1 / sqrt(1 - beta2^k) of the current step

@@ -121,7 +121,7 @@ struct Layout {
   size_t x, y, gfwd, gy, acc, loss_fwd, loss_rev, loss_iso, nn_fwd, nn_rev, edge_d, edges, e_prev, v2e_ptr, v2e;
   size_t src4, tgt4, verts4;
   size_t t_hist, t_off, t_keys, t_pts, t_csum, m_hist, m_off, m_keys, m_pts, m_csum;
-  size_t hard, hard_count, step, bias, loss, status, loss_part;
+  size_t hard, hard_count, step, bias, loss, status, loss_part, gmax;
   int tbits, mbits;
 };
 
@@ -196,6 +196,7 @@ Layout make_layout(const pdg_config& c, int V, int E, int max_pts) {
   L.bias = a.take<float>(2);
   L.loss = a.take<double>(4);
   L.status = a.take<int>(1);
+  L.gmax = a.take<unsigned>(1);
   L.total = (a.off + 255) & ~size_t(255);
   return L;
 }
@@ -544,6 +545,7 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
   J.bias = (float*)P(L.bias);
   J.loss = (double*)P(L.loss);
   J.status = (int*)P(L.status);
+  J.gmax = (unsigned*)P(L.gmax);
 
   if (n_edges) {
     if (cudaMemcpyAsync((void*)J.edges, he.data(), he.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -798,6 +800,21 @@ pdg_status pdg_write_theta(pdg_ctx* c, int level, const float* theta, void* cuda
     CU(c, cudaStreamSynchronize(s));
   }
   return c->cuda(cudaGetLastError(), "write_theta");
+}
+
+pdg_status pdg_eval(pdg_ctx* c, double* loss, void* cuda_stream) {
+  if (!c) return PDG_ERR_INVALID;
+  if (!c->in_frame) return c->fail(PDG_ERR_STATE, "pdg_eval outside a frame");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  launch_plan(c->dplan, 2, s);
+  for (int i = 1; i < N_STAGES; ++i)
+    if (i != 9 && i != 10) launch_stage(i, c->dplan, c->nmax, c->sms, s);  // no preconditioner, no Adam
+  CU(c, cudaGetLastError());
+  if (loss) {
+    CU(c, cudaMemcpyAsync(loss, c->h.loss, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(c, cudaStreamSynchronize(s));
+  }
+  return PDG_OK;
 }
 
 pdg_status pdg_precondition(pdg_ctx* c, int level, const float* g, float* out, void* cuda_stream) {
