@@ -117,10 +117,10 @@ __device__ __forceinline__ long long warp_sum(long long v) {
   return v;
 }
 
-// Rows are taken 32 at a time per warp (all levels of all jobs in one launch).  Fine levels
-// (n >= 64, a few dozen entries per row) give each lane its own row; coarse levels (hundreds
-// to thousands of entries per row) sum each of the 32 rows with the whole warp.  Both sum
-// in the same 64-bit fixed point, so the result does not depend on the split.
+// All levels of all jobs in one launch.  Fine levels (n >= 64, a few dozen to a few hundred
+// entries per row) give each warp 32 rows, one per lane; coarse levels (hundreds to
+// thousands of entries per row) give each warp one row.  Both sum in the same 64-bit fixed
+// point, so the result does not depend on the split.
 __device__ __forceinline__ void row_sum(const Level& lv, const float4* __restrict__ gy, int s, int e, int step,
                                         float sc, long long& ax, long long& ay, long long& az) {
   const int* __restrict__ ep = lv.ent_p;
@@ -147,13 +147,13 @@ __global__ void __launch_bounds__(256) k_adjoint(const Plan* __restrict__ P) {
     int l = 0, na = 0;
     for (; l < J.L; ++l) {
       na = *J.lev[l].n_active;
-      const int ng = (na + 31) >> 5;
+      const int ng = J.lev[l].n >= 64 ? (na + 31) >> 5 : na;
       if (gi < ng) break;
       gi -= ng;
     }
     if (l >= J.L) continue;
     const Level& lv = J.lev[l];
-    const int r0 = gi << 5;
+    const int r0 = lv.n >= 64 ? gi << 5 : gi;
     // fixed-point scale from the step's bound on |dL/dy|: every term |w g| < 2^ex and a row
     // has at most Q terms, so partial sums stay below 2^62
     const float gm = __uint_as_float(*J.gmax);
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(256) k_adjoint(const Plan* __restrict__ P) {
         lv.g[2 * lv.n3 + v] = finite ? __ll2float_rn(az) * isc : nan;
       }
     } else {
-      const int rend = min(r0 + 32, na);
+      const int rend = r0 + 1;
       for (int r = r0; r < rend; ++r) {
         long long ax = 0, ay = 0, az = 0;
         if (gm > 0.f && finite)

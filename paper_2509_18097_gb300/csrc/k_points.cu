@@ -33,7 +33,8 @@ __global__ void k_plan(Plan* P, int bump) {
     cnt[ST_MOVCH][j] = (2 * G * G * G + SCAN_CHUNK - 1) / SCAN_CHUNK;
     int a = 0, t = 0, p3 = 0;
     for (int l = 0; l < J->L; ++l) {
-      a += (*J->lev[l].n_active + 31) >> 5;  // adjoint: groups of 32 rows
+      // adjoint: a warp per row on coarse levels, per 32 rows on fine ones
+      a += J->lev[l].n >= 64 ? (*J->lev[l].n_active + 31) >> 5 : *J->lev[l].n_active;
       if (J->lev[l].n > 128) t += J->lev[l].tiles;
       else p3 += J->lev[l].n;
     }
