@@ -192,6 +192,30 @@ size_t pdg_state_bytes(const pdg_ctx* ctx);
 pdg_status pdg_save_state(pdg_ctx* ctx, void* host_buf, size_t n, void* cuda_stream);
 pdg_status pdg_load_state(pdg_ctx* ctx, const void* host_buf, size_t n, void* cuda_stream);
 
+/* ---- allocation-free preconditioner --------------------------------------------------
+ * The paper has no counterpart of this entry point; it exists for callers that cannot
+ * allocate device memory when they need the preconditioner: a service whose device-memory
+ * budget was fixed at start-up, a host allocator that must not be re-entered from the
+ * calling thread, or a latency-critical path on which any allocation is forbidden.
+ *
+ * out = (I + lambda L)^{-2} g per channel on a res^3 vertex grid (L the free-boundary
+ * 6-neighbour graph Laplacian), computed by the same preconditioner kernels as
+ * pdg_precondition, without a context and without allocating: its scratch lives in one
+ * fixed file-scope device array of about 6.3 MB (two res^3 x 3 float buffers at the maximum
+ * res plus small tables), which every GPU that loads the library keeps until the process
+ * exits.
+ *  - g, out: DEVICE pointers to float [res^3][3] ((z*res + y)*res + x); host pointers give
+ *    PDG_ERR_INVALID.  res: 1 or a power of two up to PDG_STATIC_MAX_RES; larger grids give
+ *    PDG_ERR_BUDGET (use pdg_precondition).  lambda: finite, >= 0.
+ *  - The first call on a device looks up the array's device address and sets the kernels'
+ *    shared-memory limits; make that first call before any stream capture.
+ *  - Every call uses the same array and leaves its contents behind (each call overwrites
+ *    everything it reads).  Calls whose work overlaps on the GPU (other streams, threads or
+ *    processes sharing the device) race on it: serialise them.
+ *  - Asynchronous on `cuda_stream`; nothing is allocated, freed or synchronised. */
+#define PDG_STATIC_MAX_RES 64
+pdg_status pdg_precondition_static(int res, float lambda, const float* g, float* out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

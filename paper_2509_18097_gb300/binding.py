@@ -80,6 +80,7 @@ _SIGS = {
     "pdg_set_debug": (C.c_int, [C.c_void_p, C.c_int]),
     "pdg_precondition": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pdg_eval": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
+    "pdg_precondition_static": (C.c_int, [C.c_int, C.c_float, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pdg_profile_stages": (C.c_int, []),
     "pdg_profile_stage_name": (C.c_char_p, [C.c_int]),
     "pdg_profile_step": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
@@ -263,6 +264,15 @@ def pdg_precondition(ctx, level: int, g, out, stream=None):
     o = _Arr(out, np.float32, 3, "out")
     _check(load().pdg_precondition(ctx, int(level), a.ptr, o.ptr, _stream(stream)), ctx)
     return out
+
+
+def pdg_precondition_static(res: int, lam: float, g, out, stream=None):
+    """Allocation-free (I + lambda L)^{-2} on a res^3 grid; g and out must be CUDA tensors
+    of shape [res^3, 3].  Returns the status code (not raised: callers of this entry point
+    typically handle errors themselves)."""
+    a = _Arr(g, np.float32, 3, "g")
+    o = _Arr(out, np.float32, 3, "out")
+    return int(load().pdg_precondition_static(int(res), float(lam), a.ptr, o.ptr, _stream(stream)))
 
 
 def pdg_set_debug(ctx, keep_pgrad: bool = True):
