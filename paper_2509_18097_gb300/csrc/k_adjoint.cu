@@ -125,13 +125,32 @@ __device__ __forceinline__ void row_sum(const Level& lv, const float4* __restric
                                         float sc, long long& ax, long long& ay, long long& az) {
   const int* __restrict__ ep = lv.ent_p;
   const float* __restrict__ ew = lv.ent_w;
-#pragma unroll 4
-  for (int k = s; k < e; k += step) {
-    const float wt = __ldg(ew + k) * sc;  // exact: sc is a power of two
+  constexpr int B = 8;  // entries in flight per lane: all index loads, then all gathers
+  int k = s;
+  for (; k + (B - 1) * step < e; k += B * step) {
+    int p[B];
+    float wt[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      p[u] = __ldg(ep + k + u * step);
+      wt[u] = __ldg(ew + k + u * step) * sc;  // exact: sc is a power of two
+    }
+    float4 g[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) g[u] = __ldg(gy + p[u]);
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      ax += __float2ll_rn(wt[u] * g[u].x);
+      ay += __float2ll_rn(wt[u] * g[u].y);
+      az += __float2ll_rn(wt[u] * g[u].z);
+    }
+  }
+  for (; k < e; k += step) {
+    const float w1 = __ldg(ew + k) * sc;
     const float4 g = __ldg(gy + __ldg(ep + k));
-    ax += __float2ll_rn(wt * g.x);
-    ay += __float2ll_rn(wt * g.y);
-    az += __float2ll_rn(wt * g.z);
+    ax += __float2ll_rn(w1 * g.x);
+    ay += __float2ll_rn(w1 * g.y);
+    az += __float2ll_rn(w1 * g.z);
   }
 }
 

@@ -26,10 +26,12 @@ struct Best {
 
 __device__ __forceinline__ void consider(Best& b, const float4 p, float qx, float qy, float qz) {
   const float d2 = sqdist(qx, qy, qz, p.x, p.y, p.z);
-  const int id = __float_as_int(p.w);
-  if (d2 < b.d2 || (d2 == b.d2 && id < b.idx)) {
-    b.d2 = d2;
-    b.idx = id;
+  if (d2 <= b.d2) {  // rarely taken; the index decides only between equal distances
+    const int id = __float_as_int(p.w);
+    if (d2 < b.d2 || id < b.idx) {
+      b.d2 = d2;
+      b.idx = id;
+    }
   }
 }
 

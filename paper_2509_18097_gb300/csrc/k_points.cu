@@ -23,8 +23,9 @@ __global__ void k_plan(Plan* P, int bump) {
     if (bump == 1) {
       int k = *J->step + 1;
       *J->step = k;
-      J->bias[0] = (float)(1.0 / (1.0 - pow((double)J->beta1, (double)k)));
-      J->bias[1] = (float)(1.0 / sqrt(1.0 - pow((double)J->beta2, (double)k)));
+      // 1 - beta^k = -expm1(k log1p(beta - 1)): no cancellation for small k (beta - 1 is exact)
+      J->bias[0] = 1.f / -expm1f((float)k * log1pf(J->beta1 - 1.f));
+      J->bias[1] = rsqrtf(-expm1f((float)k * log1pf(J->beta2 - 1.f)));
     }
     const int G = 1 << J->mov.bits;
     cnt[ST_Q][j] = J->Q;

@@ -73,7 +73,7 @@ struct pdg_ctx {
   float* stage = nullptr;  // [stage_pts][3] staging of host inputs
   int stage_pts = 0;
   int nmax = 1;
-  cudaStream_t cap = nullptr;
+  cudaStream_t cap = nullptr, cap2 = nullptr;
   cudaGraphExec_t gexec = nullptr;
   std::vector<int> v2e_ptr, v2e;
 
@@ -94,7 +94,7 @@ struct pdg_batch {
   std::vector<pdg_ctx*> members;
   Plan* dplan = nullptr;
   Plan* hplan = nullptr;  // pinned host copy
-  cudaStream_t cap = nullptr;
+  cudaStream_t cap = nullptr, cap2 = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int graph_nmax = 0;
   bool dirty = true;  // membership changed since the last upload of the job table
@@ -276,16 +276,41 @@ void launch_stage(int i, const Plan* plan, int nmax, int sms, cudaStream_t s) {
   }
 }
 
-pdg_status capture_step(pdg_ctx* c, const Plan* plan, int nmax, cudaStream_t cap, cudaGraphExec_t* out,
-                        std::string* err, int sms) {
+// Captures one step.  Two branches: the isometry kernel runs beside the nearest-neighbour
+// stages (it needs only the deformed points), the loss reduction beside the adjoint and
+// the preconditioner (nothing downstream reads it).
+pdg_status capture_step(pdg_ctx* c, const Plan* plan, int nmax, cudaStream_t cap, cudaStream_t cap2,
+                        cudaGraphExec_t* out, std::string* err, int sms) {
   cudaGraph_t g = nullptr;
+  cudaEvent_t ev[4] = {};
+  for (auto& e : ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      *err = "cudaEventCreate failed";
+      return PDG_ERR_CUDA;
+    }
   cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) {
     *err = std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e);
+    for (auto& x : ev) cudaEventDestroy(x);
     return PDG_ERR_CUDA;
   }
-  for (int i = 0; i < N_STAGES; ++i) launch_stage(i, plan, nmax, sms, cap);
+  launch_stage(0, plan, nmax, sms, cap);  // plan
+  launch_stage(1, plan, nmax, sms, cap);  // interp
+  cudaEventRecord(ev[0], cap);
+  cudaStreamWaitEvent(cap2, ev[0], 0);
+  launch_stage(6, plan, nmax, sms, cap2);  // iso_edges
+  cudaEventRecord(ev[1], cap2);
+  for (int i = 2; i <= 5; ++i) launch_stage(i, plan, nmax, sms, cap);  // moving grid, NN
+  cudaStreamWaitEvent(cap, ev[1], 0);
+  launch_stage(7, plan, nmax, sms, cap);  // assemble
+  cudaEventRecord(ev[2], cap);
+  cudaStreamWaitEvent(cap2, ev[2], 0);
+  launch_stage(11, plan, nmax, sms, cap2);  // loss
+  cudaEventRecord(ev[3], cap2);
+  for (int i = 8; i <= 10; ++i) launch_stage(i, plan, nmax, sms, cap);  // adjoint, preconditioner + Adam
+  cudaStreamWaitEvent(cap, ev[3], 0);
   e = cudaStreamEndCapture(cap, &g);
+  for (auto& x : ev) cudaEventDestroy(x);
   if (e != cudaSuccess) {
     *err = std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e);
     if (g) cudaGraphDestroy(g);
@@ -358,6 +383,7 @@ void pdg_destroy(pdg_ctx* c) {
   if (!c) return;
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->cap2) cudaStreamDestroy(c->cap2);
   if (c->arena) cudaFree(c->arena);
   delete c;
 }
@@ -572,7 +598,9 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
     if (cudaMemcpyAsync(c->dplan, &hp, sizeof(Plan), cudaMemcpyHostToDevice, s) != cudaSuccess)
       return bail(PDG_ERR_CUDA);
   }
-  if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) return bail(PDG_ERR_CUDA);
+  if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(PDG_ERR_CUDA);
   if (cudaStreamSynchronize(s) != cudaSuccess) return bail(PDG_ERR_CUDA);
   *out = c;
   return PDG_OK;
@@ -622,7 +650,7 @@ pdg_status pdg_step(pdg_ctx* c, int n_steps, void* cuda_stream) {
   if (!c->gexec) {
     // the captured launches must not start before this stream's pending set-up
     CU(c, cudaStreamSynchronize(s));
-    TRY(capture_step(c, c->dplan, c->nmax, c->cap, &c->gexec, &c->err, c->sms));
+    TRY(capture_step(c, c->dplan, c->nmax, c->cap, c->cap2, &c->gexec, &c->err, c->sms));
   }
   for (int i = 0; i < n_steps; ++i) CU(c, cudaGraphLaunch(c->gexec, s));
   c->steps_in_frame += n_steps;
@@ -860,7 +888,8 @@ pdg_status pdg_batch_create(int max_jobs, pdg_batch** out) {
   pdg_batch* b = new pdg_batch();
   b->max_jobs = max_jobs;
   if (cudaMalloc(&b->dplan, sizeof(Plan)) != cudaSuccess || cudaMallocHost(&b->hplan, sizeof(Plan)) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->cap2, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     pdg_batch_destroy(b);
     return PDG_ERR_OOM;
@@ -874,6 +903,7 @@ void pdg_batch_destroy(pdg_batch* b) {
   if (!b) return;
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->cap2) cudaStreamDestroy(b->cap2);
   if (b->dplan) cudaFree(b->dplan);
   if (b->hplan) cudaFreeHost(b->hplan);
   delete b;
@@ -924,7 +954,7 @@ pdg_status pdg_batch_step(pdg_batch* b, int n_steps, void* cuda_stream) {
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;
     if (cudaStreamSynchronize(s) != cudaSuccess) return PDG_ERR_CUDA;
-    const pdg_status st = capture_step(nullptr, b->dplan, nmax, b->cap, &b->gexec, &b->err, sms);
+    const pdg_status st = capture_step(nullptr, b->dplan, nmax, b->cap, b->cap2, &b->gexec, &b->err, sms);
     if (st != PDG_OK) return st;
     b->graph_nmax = nmax;
   }
