@@ -136,6 +136,18 @@ def candidate_flops(y, V, target, bits, lo=-1.5, hi=1.5):
     return 8.0 * float(n)
 
 
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """Max of a per-rank float over all ranks (the slowest rank defines the timed region);
+    the value itself without a process group."""
+    if dist is None:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def grid_bits(count):
     import math
 
@@ -189,6 +201,37 @@ def stage_model(stage, Q, V, M, E, res, act):
     return "hbm", 0, "B"
 
 
+# ------------------------------------------------------------------------------ serving
+
+
+def run_serving(n_seq=16, n_frames=3, steps=100, rate_hz=400.0, scale=0.2, budget_gb=150.0):
+    """Served frames/s and p50/p99 per-frame latency: continuous batching vs the plain
+    one-frame-at-a-time form, on the same Poisson trace (sequences drawn like the batched
+    workload, points per frame scaled by `scale`)."""
+    import numpy as np
+
+    from paper_2509_18097_gb300 import serve, synth
+
+    seqs = []
+    for i in range(n_seq):
+        jb = synth.batched_job(i, scale=scale)
+        frames = [jb["frame"](k, n_frames + 1) for k in range(n_frames + 1)]
+        mp = max(len(f) for f in frames)
+        seqs.append(serve.Sequence(i, jb["template"], jb["edges"], frames[0], frames[1:], jb["res"], mp))
+    out = {"sequences": n_seq, "frames": n_seq * n_frames, "steps_per_frame": steps, "rate_hz": rate_hz,
+           "points_per_frame": [int(min(len(f) for s_ in seqs for f in s_.frames)),
+                                int(max(len(f) for s_ in seqs for f in s_.frames))],
+           "finest_res": [int(min(s_.res[-1] for s_ in seqs)), int(max(s_.res[-1] for s_ in seqs))]}
+    srv = serve.Server(seqs, steps=steps, budget_bytes=int(budget_gb * 1e9), max_slots=64)
+    b = srv.run(serve.poisson_trace(seqs, rate_hz, seed=1), realtime=True)
+    srv.close()
+    p = serve.serve_plain(seqs, serve.poisson_trace(seqs, rate_hz, seed=1), steps, realtime=True)
+    for k, r in (("batched", b), ("plain", p)):
+        out[k] = {"frames_per_s": r["frames_per_s"], "p50_ms": 1e3 * r["p50_s"], "p99_ms": 1e3 * r["p99_s"],
+                  "wall_s": r["wall_s"]}
+    return out
+
+
 # ------------------------------------------------------------------------------ reference arm
 
 
@@ -230,6 +273,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=10)
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -304,11 +348,7 @@ def main():
     clocks = clk.summary()
     dev_ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
     resident_ms = e0.elapsed_time(e1) / STEPS_PER_FRAME
-    t_max = dev_ms
-    if dist is not None:
-        tt = torch.tensor([dev_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(dev_ms, dist, dev)
     value = world * args.steps / (t_max / 1000.0)
     ms_per_step = t_max / args.steps
 
@@ -355,10 +395,7 @@ def main():
     B.pdg_get_vertices(ctx, verts_host)
     t_e2e = time.perf_counter() - t0
     barrier()
-    if dist is not None:
-        tt = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+    t_e2e = max_over_ranks(t_e2e, dist, dev)
     e2e = {"value": world * STEPS_PER_FRAME_E2E / t_e2e, "unit": "steps/s",
            "h2d_bytes_per_step": M * 12 / STEPS_PER_FRAME_E2E,
            "d2h_bytes_per_step": (V * 12 + 48) / STEPS_PER_FRAME_E2E,
@@ -366,7 +403,11 @@ def main():
            "final_loss": stats.loss_total}
     B.pdg_destroy(ctx)
 
-    launches_per_step = 18
+    serving = None
+    if not args.no_serving:
+        serving = run_serving()
+
+    launches_per_step = 17  # plan, interp, 3 scan, scatter, nn, nn_hard, iso, assemble, adjoint, 3 Sobolev, 2 loss
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import pdg_oracle as O
@@ -390,7 +431,7 @@ def main():
                        "V": V, "N": N, "M": M, "E": E},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
             "roofline": roof, "cpu_baseline": cpu, "stages": stages,
-            "resident_l2_steps_per_s": 1000.0 / resident_ms, "wall_s_timed": wall,
+            "resident_l2_steps_per_s": 1000.0 / resident_ms, "wall_s_timed": wall, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -111,16 +111,10 @@ void launch_csr_build(Job* J, const Job& hJ, cudaStream_t s) {
 
 // ------------------------------------------------------------------------------ per step
 
-__device__ __forceinline__ long long warp_sum(long long v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// All levels of all jobs in one launch.  Fine levels (n >= 64, a few dozen to a few hundred
-// entries per row) give each warp 32 rows, one per lane; coarse levels (hundreds to
-// thousands of entries per row) give each warp one row.  Both sum in the same 64-bit fixed
-// point, so the result does not depend on the split.
+// All levels of all jobs in one launch.  Levels of 128^3 and finer (a few dozen entries per
+// row) give each warp 4 rows, 8 lanes per row; coarser levels (hundreds to thousands of
+// entries per row) give each warp one row.  Every lane keeps 8 gathers in flight.  All
+// partial sums are 64-bit fixed point, so the result does not depend on the split.
 __device__ __forceinline__ void row_sum(const Level& lv, const float4* __restrict__ gy, int s, int e, int step,
                                         float sc, long long& ax, long long& ay, long long& az) {
   const int* __restrict__ ep = lv.ent_p;
@@ -166,13 +160,16 @@ __global__ void __launch_bounds__(256) k_adjoint(const Plan* __restrict__ P) {
     int l = 0, na = 0;
     for (; l < J.L; ++l) {
       na = *J.lev[l].n_active;
-      const int ng = J.lev[l].n >= 64 ? (na + 31) >> 5 : na;
+      const int ng = J.lev[l].n >= 128 ? (na + 3) >> 2 : na;
       if (gi < ng) break;
       gi -= ng;
     }
     if (l >= J.L) continue;
     const Level& lv = J.lev[l];
-    const int r0 = lv.n >= 64 ? gi << 5 : gi;
+    const bool fine = lv.n >= 128;
+    const int lpr = fine ? 8 : 32;             // lanes per row
+    const int r = fine ? (gi << 2) + (lane >> 3) : gi;
+    const int sub = fine ? (lane & 7) : lane;
     // fixed-point scale from the step's bound on |dL/dy|: every term |w g| < 2^ex and a row
     // has at most Q terms, so partial sums stay below 2^62
     const float gm = __uint_as_float(*J.gmax);
@@ -184,34 +181,27 @@ __global__ void __launch_bounds__(256) k_adjoint(const Plan* __restrict__ P) {
       sh = min(62 - ex - (32 - __clz(J.Q)), 126);
     }
     const float sc = exp2f((float)sh), isc = exp2f((float)-sh);
-    if (lv.n >= 64) {
-      const int r = r0 + lane;
-      if (r < na) {
-        long long ax = 0, ay = 0, az = 0;
-        if (gm > 0.f && finite) row_sum(lv, J.gy, __ldg(lv.act_ptr + r), __ldg(lv.act_ptr + r + 1), 1, sc, ax, ay, az);
-        const int v = __ldg(lv.act_v + r);
-        const float nan = __int_as_float(0x7fc00000);
-        lv.g[v] = finite ? __ll2float_rn(ax) * isc : nan;
-        lv.g[lv.n3 + v] = finite ? __ll2float_rn(ay) * isc : nan;
-        lv.g[2 * lv.n3 + v] = finite ? __ll2float_rn(az) * isc : nan;
+    long long ax = 0, ay = 0, az = 0;
+    if (r < na && gm > 0.f && finite)
+      row_sum(lv, J.gy, __ldg(lv.act_ptr + r) + sub, __ldg(lv.act_ptr + r + 1), lpr, sc, ax, ay, az);
+    // reduce within the row's lanes (aligned groups of lpr lanes)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long tx = __shfl_xor_sync(0xffffffffu, ax, o);
+      const long long ty = __shfl_xor_sync(0xffffffffu, ay, o);
+      const long long tz = __shfl_xor_sync(0xffffffffu, az, o);
+      if (o < lpr) {
+        ax += tx;
+        ay += ty;
+        az += tz;
       }
-    } else {
-      const int rend = r0 + 1;
-      for (int r = r0; r < rend; ++r) {
-        long long ax = 0, ay = 0, az = 0;
-        if (gm > 0.f && finite)
-          row_sum(lv, J.gy, __ldg(lv.act_ptr + r) + lane, __ldg(lv.act_ptr + r + 1), 32, sc, ax, ay, az);
-        ax = warp_sum(ax);
-        ay = warp_sum(ay);
-        az = warp_sum(az);
-        if (lane == 0) {
-          const int v = __ldg(lv.act_v + r);
-          const float nan = __int_as_float(0x7fc00000);
-          lv.g[v] = finite ? __ll2float_rn(ax) * isc : nan;
-          lv.g[lv.n3 + v] = finite ? __ll2float_rn(ay) * isc : nan;
-          lv.g[2 * lv.n3 + v] = finite ? __ll2float_rn(az) * isc : nan;
-        }
-      }
+    }
+    if (sub == 0 && r < na) {
+      const int v = __ldg(lv.act_v + r);
+      const float nan = __int_as_float(0x7fc00000);
+      lv.g[v] = finite ? __ll2float_rn(ax) * isc : nan;
+      lv.g[lv.n3 + v] = finite ? __ll2float_rn(ay) * isc : nan;
+      lv.g[2 * lv.n3 + v] = finite ? __ll2float_rn(az) * isc : nan;
     }
   }
 }

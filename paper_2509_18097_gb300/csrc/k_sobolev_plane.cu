@@ -1,15 +1,17 @@
 // Grid Sobolev preconditioning (Sec. 3.2, Eq. 3) fused with Adam (Sec. 3.6) for levels of
 // up to 128^3 vertices, in three passes over shared-memory planes:
 //   A  per (z-plane, channel): DCT-II along x, then along y           g   -> tmp
-//   B  per (y-slab, channel):  DCT-II along z, spectral scale
-//                              (1 + lambda (mu_kx + mu_ky + mu_kz))^{-2} / n^3, inverse along z
+//   B  per (y-slab, channel):  for every (kx, ky) column along z, two tridiagonal solves with
+//                              T = (1 + lambda (mu_kx + mu_ky)) I + lambda L_z (T^{-2}), and the
+//                              1/n^2 of the x and y inverse transforms
 //   C  per z-plane:            inverse along y and x, then Adam on theta, m, v, channel by
 //                              channel (theta is read-modified-written per channel; its plane
 //                              stays in L2 between the three channels)
-// Why the DCT: L_l, the free-boundary 6-neighbour Laplacian, is the Kronecker sum of three
+// Why: L_l, the free-boundary 6-neighbour Laplacian, is the Kronecker sum of three
 // path-graph Laplacians whose eigenvectors are the DCT-II basis vectors
-// cos(pi k (i + 1/2) / n) with eigenvalues mu_k = 4 sin^2(pi k / 2n), so the preconditioner
-// is diagonal in the 3-D DCT basis.
+// cos(pi k (i + 1/2) / n) with eigenvalues mu_k = 4 sin^2(pi k / 2n).  After the x and y DCTs
+// the operator (I + lambda L)^{-2} acts on each (kx, ky) column along z as T^{-2} with the
+// tridiagonal T above, which the Thomas algorithm inverts exactly in O(n) per column.
 //
 // A line transform handles two lines at once (packed as the real and imaginary parts of one
 // complex sequence after the even/odd reordering that turns a DCT-II into a DFT).  The
@@ -295,9 +297,140 @@ __device__ __forceinline__ bool plane_item(const Job& J, int r, bool three, int&
   return false;
 }
 
-// pass A (PASS 0) and pass B (PASS 1): per (plane, channel)
+// Pass B: one thread per (x, y) column of a level, all three channels.  T has diagonal
+// b_i = a + lambda deg(i) (deg 1 at the two ends, 2 inside) and off-diagonal -lambda, with
+// a = 1 + lambda (mu_kx + mu_ky); it is the same for the three channels.  The first forward
+// sweep stores the reciprocal pivots r_i = 1 / (b_i + lambda c'_{i-1}) (c'_i = -lambda r_i)
+// in the level's pivot buffer; the other three sweeps reuse them.  Consecutive threads take
+// consecutive x, so every access along z is coalesced.
+__device__ __forceinline__ bool column_item(const Job& J, int r, int& l, int& col) {
+  for (l = 0; l < J.L; ++l) {
+    const int n = J.lev[l].n;
+    if (n > 128) continue;
+    if (r < n * n) {
+      col = r;
+      return true;
+    }
+    r -= n * n;
+  }
+  return false;
+}
+
+// The four Thomas sweeps of one column (three channels), in blocks of K steps: all loads
+// of a block are issued before its recursion runs, so the memory latency is paid once per
+// block rather than once per step.  n is a multiple of K.
+template <int K>
+__device__ __forceinline__ void column_solve(float* __restrict__ t0, float* __restrict__ t1, float* __restrict__ t2,
+                                             float* __restrict__ rp, int n, size_t n2, float a, float lam,
+                                             float scale) {
+  float v0[K], v1[K], v2[K], rr[K];
+  // solve 1, forward: pivots
+  float cp = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+  for (int i0 = 0; i0 < n; i0 += K) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const size_t o = (i0 + k) * n2;
+      v0[k] = t0[o]; v1[k] = t1[o]; v2[k] = t2[o];
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int i = i0 + k;
+      const float b = a + lam * ((i == 0 || i == n - 1) ? 1.f : 2.f);
+      const float r = 1.f / (b + lam * cp);
+      rr[k] = r;
+      g0 = (v0[k] + lam * g0) * r;
+      g1 = (v1[k] + lam * g1) * r;
+      g2 = (v2[k] + lam * g2) * r;
+      v0[k] = g0; v1[k] = g1; v2[k] = g2;
+      cp = -lam * r;
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const size_t o = (i0 + k) * n2;
+      t0[o] = v0[k]; t1[o] = v1[k]; t2[o] = v2[k]; rp[o] = rr[k];
+    }
+  }
+  // solve 1, backward (the last element is final); solve 2 forward follows the same blocks
+  for (int pass = 0; pass < 3; ++pass) {
+    const bool back = pass != 1;
+    const bool last = pass == 2;
+    if (!back) g0 = g1 = g2 = 0.f;
+    if (last) {  // g holds g'_{n-1} of solve 2: scale it in place
+      const size_t o = (n - 1) * n2;
+      t0[o] = g0 * scale; t1[o] = g1 * scale; t2[o] = g2 * scale;
+    }
+    for (int b = 0; b < n; b += K) {
+      const int i0 = back ? n - K - b : b;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const size_t o = (i0 + k) * n2;
+        v0[k] = t0[o]; v1[k] = t1[o]; v2[k] = t2[o]; rr[k] = rp[o];
+      }
+      if (back) {
+#pragma unroll
+        for (int k = K - 1; k >= 0; --k) {
+          if (i0 + k == n - 1) {  // h_{n-1} = g'_{n-1}
+            if (last) { v0[k] = g0 * scale; v1[k] = g1 * scale; v2[k] = g2 * scale; }
+            continue;
+          }
+          const float lr = lam * rr[k];
+          g0 = v0[k] + lr * g0;
+          g1 = v1[k] + lr * g1;
+          g2 = v2[k] + lr * g2;
+          if (last) { v0[k] = g0 * scale; v1[k] = g1 * scale; v2[k] = g2 * scale; }
+          else { v0[k] = g0; v1[k] = g1; v2[k] = g2; }
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          g0 = (v0[k] + lam * g0) * rr[k];
+          g1 = (v1[k] + lam * g1) * rr[k];
+          g2 = (v2[k] + lam * g2) * rr[k];
+          v0[k] = g0; v1[k] = g1; v2[k] = g2;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const size_t o = (i0 + k) * n2;
+        t0[o] = v0[k]; t1[o] = v1[k]; t2[o] = v2[k];
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_sobz(const Plan* __restrict__ P) {
+  const int nj = P->n_jobs;
+  const int total = P->pre[ST_COL][nj];
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+    const int j = find_job(P->pre[ST_COL], nj, it);
+    const Job& J = *P->jobs[j];
+    if (!J.precondition) continue;
+    int l, col;
+    if (!column_item(J, it - P->pre[ST_COL][j], l, col)) continue;
+    const Level& lv = J.lev[l];
+    const int n = lv.n;
+    if (n == 1) continue;  // a single vertex: T = 1
+    const size_t n2 = (size_t)n * n, n3 = lv.n3;
+    const int x = col & (n - 1), y = col >> lv.lg;
+    const float lam = lv.lam;
+    const float a = 1.f + lam * (__ldg(lv.mu + x) + __ldg(lv.mu + y));
+    const float scale = 1.f / (float)n2;  // the 1/n of the inverse x and y transforms
+    float* __restrict__ t0 = lv.tmp + col;
+    float* __restrict__ t1 = t0 + n3;
+    float* __restrict__ t2 = t1 + n3;
+    float* __restrict__ rp = lv.piv + col;
+    if (n >= 16) {
+      column_solve<16>(t0, t1, t2, rp, n, n2, a, lam, scale);
+    } else {
+      column_solve<1>(t0, t1, t2, rp, n, n2, a, lam, scale);
+    }
+  }
+}
+
+// pass A: per (z-plane, channel), DCT-II along x then y
 template <int PASS>
 __global__ void __launch_bounds__(PL_THREADS, 2) k_sobp(const Plan* __restrict__ P) {
+  static_assert(PASS == 0, "the z direction is solved by k_sobp_z");
   extern __shared__ float smem[];
   const int nj = P->n_jobs;
   const int total = P->pre[ST_PLANE][nj];
@@ -422,14 +555,13 @@ int plane_smem_max(int nmax) {
 void sobolev_plane_configure() {
   const int smem = plane_smem_max(128);
   cudaFuncSetAttribute(k_sobp<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaFuncSetAttribute(k_sobp<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaFuncSetAttribute(k_sobp_adam, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 void launch_sobolev_plane(const Plan* P, int grid, int nmax, cudaStream_t s) {
   const int smem = plane_smem_max(nmax);
   k_sobp<0><<<grid, PL_THREADS, smem, s>>>(P);
-  k_sobp<1><<<grid, PL_THREADS, smem, s>>>(P);
+  k_sobz<<<grid * 4, 256, 0, s>>>(P);
   k_sobp_adam<<<grid, PL_THREADS, smem, s>>>(P);
 }
 
