@@ -136,6 +136,33 @@ def candidate_flops(y, V, target, bits, lo=-1.5, hi=1.5):
     return 8.0 * float(n)
 
 
+# kernel of each profiled stage and the source file that defines it
+STAGE_KERNEL = {
+    "interp": ("k_interp", "k_points.cu"), "mov_scatter": ("k_mov_scatter", "k_points.cu"),
+    "nn": ("k_nn", "k_nn.cu"), "nn_hard": ("k_nn_hard", "k_nn.cu"), "adjoint": ("k_adjoint", "k_adjoint.cu"),
+    "sob_xy_fwd": ("k_sobp<0>", "k_sobolev_plane.cu"), "sob_z": ("k_sobz", "k_sobolev_plane.cu"),
+    "sob_xy_inv": ("k_sobp_inv", "k_sobolev_plane.cu"), "adam": ("k_adam", "k_sobolev_plane.cu"),
+    "iso_edges": ("k_iso_edges", "k_points.cu"),
+    "assemble": ("k_assemble", "k_points.cu"),
+}
+
+
+def measured_traffic(stage):
+    """DRAM bytes per launch of a stage's kernel from the committed ncu summary, or None if
+    there is none or the kernel's source changed since the capture."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if stage not in STAGE_KERNEL or not os.path.exists(path):
+        return None
+    kern, src = STAGE_KERNEL[stage]
+    rec = json.load(open(path)).get("kernels", {}).get(kern)
+    if not rec:
+        return None
+    h = hashlib.sha256(open(os.path.join(ROOT, "paper_2509_18097_gb300", "csrc", src), "rb").read()).hexdigest()
+    return rec["dram_bytes_per_launch"] if rec.get("source_sha256") == h else None
+
+
 def max_over_ranks(value: float, dist=None, device=None) -> float:
     """Max of a per-rank float over all ranks (the slowest rank defines the timed region);
     the value itself without a process group."""
@@ -177,9 +204,15 @@ def active_vertices(x, res, lo=-1.5, hi=1.5):
 def stage_model(stage, Q, V, M, E, res, act):
     """Algorithmic work of one launch of a stage: (bound, amount, unit).  Bytes count the
     data the operation must move once (12 B per point or grid value, 4 B per scalar)."""
-    G = sum(n**3 for n in res)
+    G = sum(n**3 for n in res if n <= 128)
     A = sum(act)
-    if stage == "sobolev":  # read g, read+write theta, m, v (Eq. 3 + Adam)
+    if stage == "sob_xy_fwd":  # read g, write the x/y spectrum
+        return "hbm", G * 24, "B"
+    if stage == "sob_z":  # read and write the spectrum once
+        return "hbm", G * 24, "B"
+    if stage == "sob_xy_inv":  # read the solved spectrum, write the preconditioned gradient
+        return "hbm", G * 24, "B"
+    if stage == "adam":  # read the preconditioned gradient, read+write theta, m, v
         return "hbm", G * (12 + 3 * 24), "B"
     if stage == "interp":  # read x, write y, read each touched grid value
         return "hbm", Q * 24 + A * 12, "B"
@@ -369,11 +402,13 @@ def main():
         peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
         achieved = amount / (prof[dom] / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": dom, "peak_note": f"FP32 {sms} SMs x 128 FMA x 2 at {sm_mhz:.0f} MHz"}
+                "traffic": measured_traffic(dom), "kernel": STAGE_KERNEL.get(dom, (dom,))[0],
+                "peak_note": f"FP32 {sms} SMs x 128 FMA x 2 at {sm_mhz:.0f} MHz (measured clock)"}
     else:
         achieved = amount / (prof[dom] / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": None, "kernel": dom, "peak_note": f"{peak_kind} copy bandwidth"}
+                "traffic": measured_traffic(dom), "kernel": STAGE_KERNEL.get(dom, (dom,))[0],
+                "algorithmic_bytes": amount, "peak_note": f"{peak_kind} copy bandwidth (burst)"}
     stages = {}
     for k, ms in prof.items():
         b_, a_, u_ = stage_model(k, Q, V, M, E, w.res, act)
@@ -407,7 +442,7 @@ def main():
     if not args.no_serving:
         serving = run_serving()
 
-    launches_per_step = 17  # plan, interp, 3 scan, scatter, nn, nn_hard, iso, assemble, adjoint, 3 Sobolev, 2 loss
+    launches_per_step = 18  # plan, interp, 3 scan, scatter, nn, nn_hard, iso, assemble, adjoint, 3 Sobolev, Adam, 2 loss
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import pdg_oracle as O

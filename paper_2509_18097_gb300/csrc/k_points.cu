@@ -32,20 +32,22 @@ __global__ void k_plan(Plan* P, int bump) {
     cnt[ST_NNQ][j] = J->Q + 2 * J->M;
     cnt[ST_E][j] = J->E;
     cnt[ST_MOVCH][j] = (2 * G * G * G + SCAN_CHUNK - 1) / SCAN_CHUNK;
-    int a = 0, t = 0, p3 = 0, cols = 0;
+    int a = 0, t = 0, p3 = 0, cols = 0, ad = 0;
     for (int l = 0; l < J->L; ++l) {
       // adjoint: a warp per row on coarse levels, per 4 rows on 128^3 and finer
       a += J->lev[l].n >= 128 ? (*J->lev[l].n_active + 3) >> 2 : *J->lev[l].n_active;
       if (J->lev[l].n > 128) t += J->lev[l].tiles;
       else {
         p3 += J->lev[l].n;
-        cols += J->lev[l].n * J->lev[l].n;
+        cols += 3 * J->lev[l].n * J->lev[l].n;
+        ad += (J->lev[l].n3 + 3) >> 2;
       }
     }
     cnt[ST_ADJ][j] = a;
     cnt[ST_TILE][j] = t;
     cnt[ST_PLANE][j] = 3 * p3;
     cnt[ST_COL][j] = cols;
+    cnt[ST_ADAM][j] = ad;
     cnt[ST_JOB][j] = 1;
     cnt[ST_LOSSCH][j] = (J->Q + 2 * J->M + J->E + LOSS_CHUNK - 1) / LOSS_CHUNK;
   }

@@ -297,105 +297,85 @@ __device__ __forceinline__ bool plane_item(const Job& J, int r, bool three, int&
   return false;
 }
 
-// Pass B: one thread per (x, y) column of a level, all three channels.  T has diagonal
-// b_i = a + lambda deg(i) (deg 1 at the two ends, 2 inside) and off-diagonal -lambda, with
-// a = 1 + lambda (mu_kx + mu_ky); it is the same for the three channels.  The first forward
-// sweep stores the reciprocal pivots r_i = 1 / (b_i + lambda c'_{i-1}) (c'_i = -lambda r_i)
-// in the level's pivot buffer; the other three sweeps reuse them.  Consecutive threads take
-// consecutive x, so every access along z is coalesced.
-__device__ __forceinline__ bool column_item(const Job& J, int r, int& l, int& col) {
-  for (l = 0; l < J.L; ++l) {
-    const int n = J.lev[l].n;
-    if (n > 128) continue;
-    if (r < n * n) {
-      col = r;
-      return true;
-    }
-    r -= n * n;
-  }
-  return false;
-}
-
-// The four Thomas sweeps of one column (three channels), in blocks of K steps: all loads
-// of a block are issued before its recursion runs, so the memory latency is paid once per
-// block rather than once per step.  n is a multiple of K.
+// The four Thomas sweeps of one column of one channel, in blocks of K steps: all loads of a
+// block are issued before its recursion runs, so the memory latency is paid once per block
+// rather than once per step.  Each channel computes the pivots of its column in its first
+// sweep (the same expression, so the same values) and keeps them in its own plane of the
+// pivot buffer, so no thread waits on another.  n is a multiple of K.
 template <int K>
-__device__ __forceinline__ void column_solve(float* __restrict__ t0, float* __restrict__ t1, float* __restrict__ t2,
-                                             float* __restrict__ rp, int n, size_t n2, float a, float lam,
-                                             float scale) {
-  float v0[K], v1[K], v2[K], rr[K];
-  // solve 1, forward: pivots
-  float cp = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-  for (int i0 = 0; i0 < n; i0 += K) {
+__device__ __forceinline__ void column_solve(float* __restrict__ t, float* __restrict__ rp, int n, size_t n2,
+                                             float a, float lam, float scale) {
+  float v[K], rr[K];
+  float cp = 0.f, g = 0.f;
+  for (int i0 = 0; i0 < n; i0 += K) {  // solve 1, forward (pivots)
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const size_t o = (i0 + k) * n2;
-      v0[k] = t0[o]; v1[k] = t1[o]; v2[k] = t2[o];
-    }
+    for (int k = 0; k < K; ++k) v[k] = t[(i0 + k) * n2];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int i = i0 + k;
       const float b = a + lam * ((i == 0 || i == n - 1) ? 1.f : 2.f);
       const float r = 1.f / (b + lam * cp);
       rr[k] = r;
-      g0 = (v0[k] + lam * g0) * r;
-      g1 = (v1[k] + lam * g1) * r;
-      g2 = (v2[k] + lam * g2) * r;
-      v0[k] = g0; v1[k] = g1; v2[k] = g2;
+      g = (v[k] + lam * g) * r;
+      v[k] = g;
       cp = -lam * r;
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const size_t o = (i0 + k) * n2;
-      t0[o] = v0[k]; t1[o] = v1[k]; t2[o] = v2[k]; rp[o] = rr[k];
+      t[(i0 + k) * n2] = v[k];
+      rp[(i0 + k) * n2] = rr[k];
     }
   }
-  // solve 1, backward (the last element is final); solve 2 forward follows the same blocks
-  for (int pass = 0; pass < 3; ++pass) {
+  for (int pass = 0; pass < 3; ++pass) {  // solve 1 backward, solve 2 forward, solve 2 backward
     const bool back = pass != 1;
     const bool last = pass == 2;
-    if (!back) g0 = g1 = g2 = 0.f;
-    if (last) {  // g holds g'_{n-1} of solve 2: scale it in place
-      const size_t o = (n - 1) * n2;
-      t0[o] = g0 * scale; t1[o] = g1 * scale; t2[o] = g2 * scale;
-    }
+    if (!back) g = 0.f;
     for (int b = 0; b < n; b += K) {
       const int i0 = back ? n - K - b : b;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        const size_t o = (i0 + k) * n2;
-        v0[k] = t0[o]; v1[k] = t1[o]; v2[k] = t2[o]; rr[k] = rp[o];
+        v[k] = t[(i0 + k) * n2];
+        rr[k] = rp[(i0 + k) * n2];
       }
       if (back) {
 #pragma unroll
         for (int k = K - 1; k >= 0; --k) {
           if (i0 + k == n - 1) {  // h_{n-1} = g'_{n-1}
-            if (last) { v0[k] = g0 * scale; v1[k] = g1 * scale; v2[k] = g2 * scale; }
+            if (last) v[k] = g * scale;
             continue;
           }
-          const float lr = lam * rr[k];
-          g0 = v0[k] + lr * g0;
-          g1 = v1[k] + lr * g1;
-          g2 = v2[k] + lr * g2;
-          if (last) { v0[k] = g0 * scale; v1[k] = g1 * scale; v2[k] = g2 * scale; }
-          else { v0[k] = g0; v1[k] = g1; v2[k] = g2; }
+          g = v[k] + lam * rr[k] * g;
+          v[k] = last ? g * scale : g;
         }
       } else {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-          g0 = (v0[k] + lam * g0) * rr[k];
-          g1 = (v1[k] + lam * g1) * rr[k];
-          g2 = (v2[k] + lam * g2) * rr[k];
-          v0[k] = g0; v1[k] = g1; v2[k] = g2;
+          g = (v[k] + lam * g) * rr[k];
+          v[k] = g;
         }
       }
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const size_t o = (i0 + k) * n2;
-        t0[o] = v0[k]; t1[o] = v1[k]; t2[o] = v2[k];
-      }
+      for (int k = 0; k < K; ++k) t[(i0 + k) * n2] = v[k];
     }
   }
+}
+
+// Pass B: one thread per (column, channel) of a level.  T has diagonal
+// b_i = a + lambda deg(i) (deg 1 at the two ends, 2 inside) and off-diagonal -lambda, with
+// a = 1 + lambda (mu_kx + mu_ky); the reciprocal pivots r_i = 1 / (b_i + lambda c'_{i-1})
+// (c'_i = -lambda r_i) of a column go to that channel's plane of the pivot buffer.
+// Consecutive threads take consecutive x, so every access along z is coalesced.
+__device__ __forceinline__ bool column_item(const Job& J, int r, int& l, int& col) {
+  for (l = 0; l < J.L; ++l) {
+    const int n = J.lev[l].n;
+    if (n > 128) continue;
+    if (r < 3 * n * n) {
+      col = r;
+      return true;
+    }
+    r -= 3 * n * n;
+  }
+  return false;
 }
 
 __global__ void __launch_bounds__(256) k_sobz(const Plan* __restrict__ P) {
@@ -405,25 +385,21 @@ __global__ void __launch_bounds__(256) k_sobz(const Plan* __restrict__ P) {
     const int j = find_job(P->pre[ST_COL], nj, it);
     const Job& J = *P->jobs[j];
     if (!J.precondition) continue;
-    int l, col;
-    if (!column_item(J, it - P->pre[ST_COL][j], l, col)) continue;
+    int l, cc;
+    if (!column_item(J, it - P->pre[ST_COL][j], l, cc)) continue;
     const Level& lv = J.lev[l];
     const int n = lv.n;
     if (n == 1) continue;  // a single vertex: T = 1
     const size_t n2 = (size_t)n * n, n3 = lv.n3;
+    const int c = cc >> (2 * lv.lg), col = cc & (int)(n2 - 1);
     const int x = col & (n - 1), y = col >> lv.lg;
     const float lam = lv.lam;
     const float a = 1.f + lam * (__ldg(lv.mu + x) + __ldg(lv.mu + y));
     const float scale = 1.f / (float)n2;  // the 1/n of the inverse x and y transforms
-    float* __restrict__ t0 = lv.tmp + col;
-    float* __restrict__ t1 = t0 + n3;
-    float* __restrict__ t2 = t1 + n3;
-    float* __restrict__ rp = lv.piv + col;
-    if (n >= 16) {
-      column_solve<16>(t0, t1, t2, rp, n, n2, a, lam, scale);
-    } else {
-      column_solve<1>(t0, t1, t2, rp, n, n2, a, lam, scale);
-    }
+    float* __restrict__ t = lv.tmp + (size_t)c * n3 + col;
+    float* __restrict__ rp = lv.piv + (size_t)c * n3 + col;
+    if (n >= 8) column_solve<8>(t, rp, n, n2, a, lam, scale);
+    else column_solve<1>(t, rp, n, n2, a, lam, scale);
   }
 }
 
@@ -455,6 +431,14 @@ __global__ void __launch_bounds__(PL_THREADS, 2) k_sobp(const Plan* __restrict__
     const size_t rstride = PASS == 0 ? (size_t)n : (size_t)n * n;
     plane_load(plane, (PASS == 0 ? lv.g : lv.tmp) + off, n, lg, rstride);
     __syncthreads();
+    // the gradient lives on the vertices near the data: a plane that is all zero stays zero
+    bool any = false;
+    for (int e = threadIdx.x; e < n * n && !any; e += PL_THREADS) any = plane[(e >> lg) * S + (e & (n - 1))] != 0.f;
+    if (!__syncthreads_or(any)) {
+      plane_store(lv.tmp + off, plane, n, lg, rstride);
+      __syncthreads();
+      continue;
+    }
     if (PASS == 0) {
       plane_lines_n<0>(n, plane, S, 1, scr, lv, 0);  // x-lines (rows)
       __syncthreads();
@@ -468,9 +452,9 @@ __global__ void __launch_bounds__(PL_THREADS, 2) k_sobp(const Plan* __restrict__
   }
 }
 
-// pass C: per (z-plane, channel): inverse along y and x, then Adam on that channel (theta
-// keeps x, y, z in one float4; each channel's item writes only its own component)
-__global__ void __launch_bounds__(PL_THREADS, 2) k_sobp_adam(const Plan* __restrict__ P) {
+// pass C: per (z-plane, channel): inverse along y and x; the preconditioned gradient goes
+// back to tmp for the Adam kernel
+__global__ void __launch_bounds__(PL_THREADS, 2) k_sobp_inv(const Plan* __restrict__ P) {
   extern __shared__ float smem[];
   const int nj = P->n_jobs;
   const int total = P->pre[ST_PLANE][nj];
@@ -480,68 +464,94 @@ __global__ void __launch_bounds__(PL_THREADS, 2) k_sobp_adam(const Plan* __restr
     int l, idx;
     if (!plane_item(J, it - P->pre[ST_PLANE][j], true, l, idx)) continue;
     const Level& lv = J.lev[l];
-    const bool pre = J.precondition != 0;
+    if (!J.precondition) continue;  // Adam then reads the raw gradient
     const int n = lv.n, n3 = lv.n3, lg = lv.lg;
     const int c = idx >> lg, z = idx & (n - 1);
     const int S = n + 1;
     float* plane = smem;
     float2* scr = reinterpret_cast<float2*>(smem + ((n * S + 1) & ~1));
     const size_t base = (size_t)z * n * n;
-    plane_load(plane, (pre ? lv.tmp : lv.g) + (size_t)c * n3 + base, n, lg, n);
+    plane_load(plane, lv.tmp + (size_t)c * n3 + base, n, lg, n);
     __syncthreads();
-    if (pre && n > 1) {
+    if (n > 1) {
       plane_lines_n<1>(n, plane, 1, S, scr, lv, 0);  // y-lines
       __syncthreads();
       plane_lines_n<1>(n, plane, S, 1, scr, lv, 0);  // x-lines
       __syncthreads();
     }
-    float* __restrict__ mc = lv.m + (size_t)c * n3 + base;
-    float* __restrict__ vc = lv.v + (size_t)c * n3 + base;
-    float* __restrict__ th = reinterpret_cast<float*>(lv.theta + base) + c;
-    float* __restrict__ pg = lv.tmp + (size_t)c * n3 + base;
+    plane_store(lv.tmp + (size_t)c * n3 + base, plane, n, lg, n);  // the preconditioned gradient
+    __syncthreads();
+  }
+}
+
+// Adam (PyTorch semantics) on every vertex of every level (n <= 128) from the preconditioned
+// gradient in tmp (or the raw gradient without preconditioning): 4 vertices per thread,
+// float4 loads of the three channel planes of g, m and v, float4 theta.
+__device__ __forceinline__ bool adam_item(const Job& J, int r, int& l, int& q) {
+  for (l = 0; l < J.L; ++l) {
+    const int n = J.lev[l].n;
+    if (n > 128) continue;
+    const int cnt = (J.lev[l].n3 + 3) >> 2;
+    if (r < cnt) {
+      q = r;
+      return true;
+    }
+    r -= cnt;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(256) k_adam(const Plan* __restrict__ P) {
+  const int nj = P->n_jobs;
+  const int total = P->pre[ST_ADAM][nj];
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+    const int j = find_job(P->pre[ST_ADAM], nj, it);
+    const Job& J = *P->jobs[j];
+    if (J.no_adam) continue;
+    int l, q;
+    if (!adam_item(J, it - P->pre[ST_ADAM][j], l, q)) continue;
+    const Level& lv = J.lev[l];
+    const size_t n3 = lv.n3;
+    const float* __restrict__ gsrc = J.precondition ? lv.tmp : lv.g;
     const float b1 = J.beta1, b2 = J.beta2, eps = J.eps;
     const float step = lv.lr * J.bias[0];
     const float ib2 = J.bias[1];
-    const bool keep = J.keep_pgrad != 0, adam = J.no_adam == 0;
-    if (n >= 4) {
-      const int nq = (n * n) >> 2;
-#pragma unroll 2
-      for (int i = threadIdx.x; i < nq; i += PL_THREADS) {
-        const int e = i << 2;
-        const float* sp = plane + (e >> lg) * S + (e & (n - 1));
-        const float g[4] = {sp[0], sp[1], sp[2], sp[3]};
-        if (keep) *reinterpret_cast<float4*>(pg + e) = make_float4(g[0], g[1], g[2], g[3]);
-        if (!adam) continue;
-        float4 m4 = *reinterpret_cast<const float4*>(mc + e);
-        float4 v4 = *reinterpret_cast<const float4*>(vc + e);
-        float t[4] = {th[4 * (size_t)e], th[4 * (size_t)e + 4], th[4 * (size_t)e + 8], th[4 * (size_t)e + 12]};
+    if (n3 >= 4) {
+      const size_t e = (size_t)q << 2;
+      float4 th[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) th[k] = lv.theta[e + k];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float4 g4 = *reinterpret_cast<const float4*>(gsrc + c * n3 + e);
+        float4 m4 = *reinterpret_cast<const float4*>(lv.m + c * n3 + e);
+        float4 v4 = *reinterpret_cast<const float4*>(lv.v + c * n3 + e);
+        const float g[4] = {g4.x, g4.y, g4.z, g4.w};
         float* mm = &m4.x;
         float* vv = &v4.x;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           mm[k] = b1 * mm[k] + (1.f - b1) * g[k];
           vv[k] = b2 * vv[k] + (1.f - b2) * g[k] * g[k];
-          t[k] -= step * mm[k] / (sqrtf(vv[k]) * ib2 + eps);
+          (&th[k].x)[c] -= step * mm[k] / (sqrtf(vv[k]) * ib2 + eps);
         }
-        *reinterpret_cast<float4*>(mc + e) = m4;
-        *reinterpret_cast<float4*>(vc + e) = v4;
+        *reinterpret_cast<float4*>(lv.m + c * n3 + e) = m4;
+        *reinterpret_cast<float4*>(lv.v + c * n3 + e) = v4;
+      }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) th[4 * (size_t)(e + k)] = t[k];
+      for (int k = 0; k < 4; ++k) lv.theta[e + k] = th[k];
+    } else {  // n == 1
+      float4 th = lv.theta[0];
+      for (int c = 0; c < 3; ++c) {
+        const float g = gsrc[c * n3];
+        float m = b1 * lv.m[c * n3] + (1.f - b1) * g;
+        float v = b2 * lv.v[c * n3] + (1.f - b2) * g * g;
+        lv.m[c * n3] = m;
+        lv.v[c * n3] = v;
+        (&th.x)[c] -= step * m / (sqrtf(v) * ib2 + eps);
       }
-    } else {
-      for (int e = threadIdx.x; e < n * n; e += PL_THREADS) {
-        const float g = plane[(e >> lg) * S + (e & (n - 1))];
-        if (keep) pg[e] = g;
-        if (!adam) continue;
-        float m = mc[e], vv = vc[e];
-        m = b1 * m + (1.f - b1) * g;
-        vv = b2 * vv + (1.f - b2) * g * g;
-        mc[e] = m;
-        vc[e] = vv;
-        th[4 * (size_t)e] -= step * m / (sqrtf(vv) * ib2 + eps);
-      }
+      lv.theta[0] = th;
     }
-    __syncthreads();
   }
 }
 
@@ -555,14 +565,16 @@ int plane_smem_max(int nmax) {
 void sobolev_plane_configure() {
   const int smem = plane_smem_max(128);
   cudaFuncSetAttribute(k_sobp<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaFuncSetAttribute(k_sobp_adam, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_sobp_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
-void launch_sobolev_plane(const Plan* P, int grid, int nmax, cudaStream_t s) {
+// part: 0 xy-forward, 1 z solve, 2 xy-inverse, 3 Adam, -1 all four
+void launch_sobolev_plane(const Plan* P, int grid, int nmax, cudaStream_t s, int part) {
   const int smem = plane_smem_max(nmax);
-  k_sobp<0><<<grid, PL_THREADS, smem, s>>>(P);
-  k_sobz<<<grid * 4, 256, 0, s>>>(P);
-  k_sobp_adam<<<grid, PL_THREADS, smem, s>>>(P);
+  if (part < 0 || part == 0) k_sobp<0><<<grid, PL_THREADS, smem, s>>>(P);
+  if (part < 0 || part == 1) k_sobz<<<grid * 4, 256, 0, s>>>(P);
+  if (part < 0 || part == 2) k_sobp_inv<<<grid, PL_THREADS, smem, s>>>(P);
+  if (part < 0 || part == 3) k_adam<<<grid * 8, 256, 0, s>>>(P);
 }
 
 }  // namespace pdg

@@ -51,7 +51,7 @@ struct Level {
   float* v;       // [3][n3] Adam second moment
   float* g;       // [3][n3] dLoss/dTheta (zero at vertices no point touches)
   float* tmp;     // [3][n3] spectral work array (and preconditioned gradient in debug mode)
-  float* piv;     // [n3] reciprocal pivots of the z-direction tridiagonal solves (n <= 128)
+  float* piv;     // [3][n3] reciprocal pivots of the z-direction tridiagonal solves (n <= 128)
   float* mu;      // [n] eigenvalues 4 sin^2(pi k / 2n) of the 1-D path Laplacian
   float2* tw;     // [n] FFT twiddles exp(-2 pi i k / n)
   float2* tw4;    // [n] DCT twiddles exp(-i pi k / 2n)
@@ -107,7 +107,7 @@ struct Job {
   int* status;             // sticky error flags (1: non-finite loss)
 };
 
-enum Stage { ST_Q = 0, ST_NNQ, ST_E, ST_MOVCH, ST_ADJ, ST_TILE, ST_JOB, ST_LOSSCH, ST_PLANE, ST_COL, NSTAGE };
+enum Stage { ST_Q = 0, ST_NNQ, ST_E, ST_MOVCH, ST_ADJ, ST_TILE, ST_JOB, ST_LOSSCH, ST_PLANE, ST_COL, ST_ADAM, NSTAGE };
 
 struct Plan {
   int n_jobs;

@@ -145,7 +145,7 @@ Layout make_layout(const pdg_config& c, int V, int E, int max_pts) {
     v.v = a.take<float>(3 * n3);
     v.g = a.take<float>(3 * n3);
     v.tmp = a.take<float>(3 * n3);
-    v.piv = a.take<float>(n <= 128 ? n3 : 1);
+    v.piv = a.take<float>(n <= 128 ? 3 * n3 : 1);
     v.mu = a.take<float>(n);
     v.tw = a.take<float2>(n);
     v.tw4 = a.take<float2>(n);
@@ -245,9 +245,9 @@ pdg_status upload_job(pdg_ctx* c, cudaStream_t s) {
 
 // The step as an explicit list of stages; the graph capture and the profiling path launch
 // exactly the same sequence.
-const char* const STAGE_NAMES[] = {"plan",     "interp",   "mov_scan", "mov_scatter",   "nn",
-                                   "nn_hard",  "iso_edges", "assemble", "adjoint",       "sobolev",
-                                   "sobolev_256", "loss"};
+const char* const STAGE_NAMES[] = {"plan",      "interp",    "mov_scan",    "mov_scatter",    "nn",
+                                   "nn_hard",   "iso_edges", "assemble",    "adjoint",        "sob_xy_fwd",
+                                   "sob_z",     "sob_xy_inv", "adam",     "sobolev_256",    "loss"};
 constexpr int N_STAGES = sizeof(STAGE_NAMES) / sizeof(STAGE_NAMES[0]);
 
 void launch_stage(int i, const Plan* plan, int nmax, int sms, cudaStream_t s) {
@@ -264,16 +264,19 @@ void launch_stage(int i, const Plan* plan, int nmax, int sms, cudaStream_t s) {
     case 6: launch_iso_edges(plan, grid, s); break;
     case 7: launch_assemble(plan, grid, s); break;
     case 8: launch_adjoint(plan, grid, s); break;
-    case 9: {
+    case 9:
+    case 10:
+    case 11:
+    case 12: {
       const int ps = plane_smem_max(nmax);
       const int per_sm = std::max(1, std::min(8, (227 * 1024) / ps));
-      launch_sobolev_plane(plan, sms * per_sm, nmax, s);
+      launch_sobolev_plane(plan, sms * per_sm, nmax, s, i - 9);
       break;
     }
-    case 10:
+    case 13:
       if (nmax > 128) launch_sobolev_tiles(plan, sms * tiles_per_sm, nmax, s);
       break;
-    case 11: launch_loss(plan, sms * 2, s); break;
+    case 14: launch_loss(plan, sms * 2, s); break;
   }
 }
 
@@ -306,9 +309,9 @@ pdg_status capture_step(pdg_ctx* c, const Plan* plan, int nmax, cudaStream_t cap
   launch_stage(7, plan, nmax, sms, cap);  // assemble
   cudaEventRecord(ev[2], cap);
   cudaStreamWaitEvent(cap2, ev[2], 0);
-  launch_stage(11, plan, nmax, sms, cap2);  // loss
+  launch_stage(14, plan, nmax, sms, cap2);  // loss
   cudaEventRecord(ev[3], cap2);
-  for (int i = 8; i <= 10; ++i) launch_stage(i, plan, nmax, sms, cap);  // adjoint, preconditioner + Adam
+  for (int i = 8; i <= 13; ++i) launch_stage(i, plan, nmax, sms, cap);  // adjoint, preconditioner, Adam
   cudaStreamWaitEvent(cap, ev[3], 0);
   e = cudaStreamEndCapture(cap, &g);
   for (auto& x : ev) cudaEventDestroy(x);
@@ -799,7 +802,9 @@ pdg_status pdg_read(pdg_ctx* c, int which, int level, void* out, size_t out_byte
   switch (which) {
     case PDG_BUF_THETA: launch_unpack4(J.lev[level].theta, tmp, J.lev[level].n3, s); break;
     case PDG_BUF_GRAD: launch_soa_to_aos(J.lev[level].g, tmp, J.lev[level].n3, s); break;
-    case PDG_BUF_PGRAD: launch_soa_to_aos(J.lev[level].tmp, tmp, J.lev[level].n3, s); break;
+    case PDG_BUF_PGRAD:  // without the preconditioner Adam takes the raw gradient
+      launch_soa_to_aos(J.precondition ? J.lev[level].tmp : J.lev[level].g, tmp, J.lev[level].n3, s);
+      break;
     case PDG_BUF_Y: launch_unpack4(J.y, tmp, J.Q, s); break;
     case PDG_BUF_POINT_GRAD: launch_unpack4(J.gy, tmp, J.Q, s); break;
     case PDG_BUF_SOURCE: launch_unpack4(J.src4, tmp, J.N, s); break;
@@ -838,7 +843,7 @@ pdg_status pdg_eval(pdg_ctx* c, double* loss, void* cuda_stream) {
   cudaStream_t s = (cudaStream_t)cuda_stream;
   launch_plan(c->dplan, 2, s);
   for (int i = 1; i < N_STAGES; ++i)
-    if (i != 9 && i != 10) launch_stage(i, c->dplan, c->nmax, c->sms, s);  // no preconditioner, no Adam
+    if (i < 9 || i > 13) launch_stage(i, c->dplan, c->nmax, c->sms, s);  // no preconditioner, no Adam
   CU(c, cudaGetLastError());
   if (loss) {
     CU(c, cudaMemcpyAsync(loss, c->h.loss, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -872,8 +877,7 @@ pdg_status pdg_precondition(pdg_ctx* c, int level, const float* g, float* out, v
   CU(c, cudaMemcpyAsync(c->op_job, &oj, sizeof(Job), cudaMemcpyHostToDevice, s));
   CU(c, cudaMemcpyAsync(c->op_plan, &op, sizeof(Plan), cudaMemcpyHostToDevice, s));
   launch_plan(c->op_plan, 0, s);
-  launch_stage(9, c->op_plan, lv.n, c->sms, s);
-  launch_stage(10, c->op_plan, lv.n, c->sms, s);
+  for (int i = 9; i <= 13; ++i) launch_stage(i, c->op_plan, lv.n, c->sms, s);
   launch_soa_to_aos(lv.tmp, tmp, lv.n3, s);
   CU(c, cudaGetLastError());
   const pdg_status st = copy_out(c, out, tmp, bytes, s);
