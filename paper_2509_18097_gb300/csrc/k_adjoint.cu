@@ -111,98 +111,154 @@ void launch_csr_build(Job* J, const Job& hJ, cudaStream_t s) {
 
 // ------------------------------------------------------------------------------ per step
 
-// All levels of all jobs in one launch.  Levels of 128^3 and finer (a few dozen entries per
-// row) give each warp 4 rows, 8 lanes per row; coarser levels (hundreds to thousands of
-// entries per row) give each warp one row.  Every lane keeps 8 gathers in flight.  All
-// partial sums are 64-bit fixed point, so the result does not depend on the split.
+// All levels of all jobs in one launch of 256-thread blocks.  Rows are summed by groups of
+// 2^adj_lg lanes, set by the plan kernel from the level's mean row length (a few dozen
+// entries per row on 128^3, thousands on 16^3): 32 >> adj_lg rows per warp, or a whole
+// block per row on levels whose rows average 512 entries or more.  A job's items are its
+// block rows first, then its warp groups, 8 to a block.  Each lane takes its entries in
+// batches of 8: the 8 index and weight loads, then the 8 gathers, all issued before any of
+// them is used (entries past the row's end get weight 0), so a lane waits for memory twice
+// per batch however short its row.  All partial sums are 64-bit fixed point, so the result
+// does not depend on the split.
+// Round-to-nearest-even of x to an integer, exactly as a float -> int64 conversion, for
+// |x| < 2^44, using only FP32 adds and integer subtracts (the direct conversion runs on
+// the FP64 pipe, which is narrow on this part).  x + 1.5 2^45 lies in [2^45, 2^46), where
+// the spacing of floats is 2^22, so hi = (x + 1.5 2^45) - 1.5 2^45 is x rounded to a
+// multiple of 2^22 and lo = x - hi (|lo| <= 2^21) is exact.  For |v| <= 2^22, v + 1.5 2^23
+// lies in [2^23, 2^24) with spacing 1, so its bit pattern minus that of 1.5 2^23 is v
+// rounded to an integer.  hi is even, so rounding lo rounds x the same way on ties.
+__device__ __forceinline__ long long round_to_ll(float x) {
+  const float kHi = 52776558133248.0f;  // 1.5 * 2^45
+  const float kLo = 12582912.0f;        // 1.5 * 2^23
+  const float hi = __fsub_rn(__fadd_rn(x, kHi), kHi);
+  const float lo = __fsub_rn(x, hi);
+  const int li = __float_as_int(__fadd_rn(lo, kLo)) - __float_as_int(kLo);
+  const int hq = __float_as_int(__fadd_rn(__fmul_rn(hi, 2.384185791015625e-07f), kLo)) - __float_as_int(kLo);
+  return ((long long)hq << 22) + li;
+}
+
 __device__ __forceinline__ void row_sum(const Level& lv, const float4* __restrict__ gy, int s, int e, int step,
                                         float sc, long long& ax, long long& ay, long long& az) {
   const int* __restrict__ ep = lv.ent_p;
   const float* __restrict__ ew = lv.ent_w;
-  constexpr int B = 8;  // entries in flight per lane: all index loads, then all gathers
-  int k = s;
-  for (; k + (B - 1) * step < e; k += B * step) {
+  constexpr int B = 8;
+  for (int k = s; k < e; k += B * step) {
     int p[B];
     float wt[B];
 #pragma unroll
     for (int u = 0; u < B; ++u) {
-      p[u] = __ldg(ep + k + u * step);
-      wt[u] = __ldg(ew + k + u * step) * sc;  // exact: sc is a power of two
+      const int kk = min(k + u * step, e - 1);  // past the end: reload the last entry, weight 0
+      p[u] = __ldg(ep + kk);
+      wt[u] = k + u * step < e ? __ldg(ew + kk) * sc : 0.f;  // exact: sc is a power of two
     }
     float4 g[B];
 #pragma unroll
     for (int u = 0; u < B; ++u) g[u] = __ldg(gy + p[u]);
 #pragma unroll
     for (int u = 0; u < B; ++u) {
-      ax += __float2ll_rn(wt[u] * g[u].x);
-      ay += __float2ll_rn(wt[u] * g[u].y);
-      az += __float2ll_rn(wt[u] * g[u].z);
+      ax += round_to_ll(__fmul_rn(wt[u], g[u].x));
+      ay += round_to_ll(__fmul_rn(wt[u], g[u].y));
+      az += round_to_ll(__fmul_rn(wt[u], g[u].z));
     }
-  }
-  for (; k < e; k += step) {
-    const float w1 = __ldg(ew + k) * sc;
-    const float4 g = __ldg(gy + __ldg(ep + k));
-    ax += __float2ll_rn(w1 * g.x);
-    ay += __float2ll_rn(w1 * g.y);
-    az += __float2ll_rn(w1 * g.z);
   }
 }
 
-__global__ void __launch_bounds__(256) k_adjoint(const Plan* __restrict__ P) {
+// sum over aligned groups of `width` lanes (a power of two); every lane gets its group's sum
+__device__ __forceinline__ void group_sum(long long& ax, long long& ay, long long& az, int width) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long tx = __shfl_xor_sync(0xffffffffu, ax, o);
+    const long long ty = __shfl_xor_sync(0xffffffffu, ay, o);
+    const long long tz = __shfl_xor_sync(0xffffffffu, az, o);
+    if (o < width) {
+      ax += tx;
+      ay += ty;
+      az += tz;
+    }
+  }
+}
+
+__device__ __forceinline__ void store_row(const Level& lv, int r, bool finite, float isc, long long ax, long long ay,
+                                          long long az) {
+  const int v = __ldg(lv.act_v + r);
+  const float nan = __int_as_float(0x7fc00000);
+  lv.g[v] = finite ? __ll2float_rn(ax) * isc : nan;
+  lv.g[lv.n3 + v] = finite ? __ll2float_rn(ay) * isc : nan;
+  lv.g[2 * lv.n3 + v] = finite ? __ll2float_rn(az) * isc : nan;
+}
+
+__global__ void __launch_bounds__(256, 4) k_adjoint(const Plan* __restrict__ P) {
+  __shared__ long long red[3][8];
   const int nj = P->n_jobs;
   const int total = P->pre[ST_ADJ][nj];
-  const int lane = threadIdx.x & 31;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nwarps) {
-    const int j = find_job(P->pre[ST_ADJ], nj, w);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {  // block-uniform
+    const int j = find_job(P->pre[ST_ADJ], nj, it);
     const Job& J = *P->jobs[j];
-    int gi = w - P->pre[ST_ADJ][j];
-    int l = 0, na = 0;
+    int i = it - P->pre[ST_ADJ][j];
+    // fixed-point scale from the step's bound on |dL/dy|: every term |w g| < 2^ex, so a
+    // scaled term is below 2^44 (the range of round_to_ll), and a row has at most Q terms,
+    // so partial sums stay below 2^62
+    const float gm = __uint_as_float(*J.gmax);
+    const bool finite = gm <= 3.0e38f;
+    const bool live = gm > 0.f && finite;
+    int sh = 0;
+    if (live) {  // ex: gm = m 2^ex with m in [0.5, 1), as frexp
+      const unsigned gb = __float_as_uint(gm);
+      const int be = (int)(gb >> 23);
+      const int ex = be ? be - 126 : (31 - __clz((int)(gb & 0x7fffffu))) - 148;
+      sh = min(min(62 - (32 - __clz(J.Q)), 44) - ex, 126);
+    }
+    const float sc = exp2f((float)sh), isc = exp2f((float)-sh);
+    // block rows
+    int l = 0;
     for (; l < J.L; ++l) {
+      if (J.lev[l].adj_lg != 6) continue;
+      const int na = *J.lev[l].n_active;
+      if (i < na) break;
+      i -= na;
+    }
+    if (l < J.L) {
+      const Level& lv = J.lev[l];
+      long long ax = 0, ay = 0, az = 0;
+      if (live) row_sum(lv, J.gy, __ldg(lv.act_ptr + i) + threadIdx.x, __ldg(lv.act_ptr + i + 1), 256, sc, ax, ay, az);
+      group_sum(ax, ay, az, 32);
+      if (lane == 0) {
+        red[0][warp] = ax;
+        red[1][warp] = ay;
+        red[2][warp] = az;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        for (int k = 1; k < 8; ++k) {
+          ax += red[0][k];
+          ay += red[1][k];
+          az += red[2][k];
+        }
+        store_row(lv, i, finite, isc, ax, ay, az);
+      }
+      __syncthreads();
+      continue;
+    }
+    // warp groups
+    int gi = i * 8 + warp, na = 0, lg = 0;
+    for (l = 0; l < J.L; ++l) {
+      lg = J.lev[l].adj_lg;
+      if (lg == 6) continue;
       na = *J.lev[l].n_active;
-      const int ng = J.lev[l].n >= 128 ? (na + 3) >> 2 : na;
+      const int ng = (na + (32 >> lg) - 1) >> (5 - lg);
       if (gi < ng) break;
       gi -= ng;
     }
-    if (l >= J.L) continue;
+    if (l >= J.L) continue;  // past the last group (whole warp)
     const Level& lv = J.lev[l];
-    const bool fine = lv.n >= 128;
-    const int lpr = fine ? 8 : 32;             // lanes per row
-    const int r = fine ? (gi << 2) + (lane >> 3) : gi;
-    const int sub = fine ? (lane & 7) : lane;
-    // fixed-point scale from the step's bound on |dL/dy|: every term |w g| < 2^ex and a row
-    // has at most Q terms, so partial sums stay below 2^62
-    const float gm = __uint_as_float(*J.gmax);
-    const bool finite = gm <= 3.0e38f;
-    int sh = 0;
-    if (gm > 0.f && finite) {
-      int ex;
-      frexpf(gm, &ex);
-      sh = min(62 - ex - (32 - __clz(J.Q)), 126);
-    }
-    const float sc = exp2f((float)sh), isc = exp2f((float)-sh);
+    const int lpr = 1 << lg;
+    const int r = (gi << (5 - lg)) + (lane >> lg);
+    const int sub = lane & (lpr - 1);
     long long ax = 0, ay = 0, az = 0;
-    if (r < na && gm > 0.f && finite)
-      row_sum(lv, J.gy, __ldg(lv.act_ptr + r) + sub, __ldg(lv.act_ptr + r + 1), lpr, sc, ax, ay, az);
-    // reduce within the row's lanes (aligned groups of lpr lanes)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const long long tx = __shfl_xor_sync(0xffffffffu, ax, o);
-      const long long ty = __shfl_xor_sync(0xffffffffu, ay, o);
-      const long long tz = __shfl_xor_sync(0xffffffffu, az, o);
-      if (o < lpr) {
-        ax += tx;
-        ay += ty;
-        az += tz;
-      }
-    }
-    if (sub == 0 && r < na) {
-      const int v = __ldg(lv.act_v + r);
-      const float nan = __int_as_float(0x7fc00000);
-      lv.g[v] = finite ? __ll2float_rn(ax) * isc : nan;
-      lv.g[lv.n3 + v] = finite ? __ll2float_rn(ay) * isc : nan;
-      lv.g[2 * lv.n3 + v] = finite ? __ll2float_rn(az) * isc : nan;
-    }
+    if (r < na && live) row_sum(lv, J.gy, __ldg(lv.act_ptr + r) + sub, __ldg(lv.act_ptr + r + 1), lpr, sc, ax, ay, az);
+    group_sum(ax, ay, az, lpr);
+    if (sub == 0 && r < na) store_row(lv, r, finite, isc, ax, ay, az);
   }
 }
 

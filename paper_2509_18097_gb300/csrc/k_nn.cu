@@ -5,7 +5,8 @@
 // The target (per frame) and the moving sets (per step) are counting-sorted into uniform
 // cell grids (see CellGrid).  A first kernel searches every query's 3x3x3 cell box with
 // one thread per query, queries taken in cell order so neighbouring lanes read the same
-// cells.  The answer is certified when the best squared distance is below the squared
+// cells (cells that cannot beat the best distance found so far are skipped).  The answer is
+// certified when the best squared distance is below the squared
 // distance from the query to the box's open faces (with a margin covering the rounding of
 // the cell assignment); otherwise the query is appended to a per-job list that a second,
 // warp-cooperative kernel searches ring by ring (lanes split the rows of each shell, a
@@ -54,6 +55,30 @@ __device__ __forceinline__ float outside_bound2(const CellGrid& g, float qx, flo
   d -= 1e-4f * hmin;  // cell assignment and face positions are rounded in fp32
   if (d <= 0.f) return 0.f;
   return d * d * (1.f - 4e-6f);
+}
+
+// Squared lower bounds on the distance from q to any point assigned to the cell one step
+// below (m) or above (p) the query's cell along each axis: the distance to the shared face,
+// less the same rounding margin as above, squared and shrunk by the relative rounding of a
+// squared distance.  A bound over several axes is the sum of theirs.
+struct FaceBounds {
+  float m[3], p[3];
+};
+
+__device__ __forceinline__ FaceBounds face_bounds(const CellGrid& g, float qx, float qy, float qz, int cx, int cy,
+                                                  int cz) {
+  const float q[3] = {qx, qy, qz};
+  const int c[3] = {cx, cy, cz};
+  const float margin = 1e-4f * fminf(g.h[0], fminf(g.h[1], g.h[2]));
+  FaceBounds f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float dm = fmaxf(q[a] - (g.lo[a] + (float)c[a] * g.h[a]) - margin, 0.f);
+    const float dp = fmaxf((g.lo[a] + (float)(c[a] + 1) * g.h[a]) - q[a] - margin, 0.f);
+    f.m[a] = dm * dm * (1.f - 4e-6f);
+    f.p[a] = dp * dp * (1.f - 4e-6f);
+  }
+  return f;
 }
 
 // ------------------------------------------------------------------------------ finalise
@@ -162,14 +187,35 @@ __global__ void __launch_bounds__(256) k_nn(const Plan* __restrict__ P) {
     const int cy = cell_coord(q.y, g.lo[1], g.inv_h[1], G);
     const int cz = cell_coord(q.z, g.lo[2], g.inv_h[2], G);
     Best b{FLT_MAX, 0x7fffffff};
-    // ring 1: the 3x3x3 box as 9 x-rows
+    // ring 1: the 3x3x3 box, the query's own cell first.  A neighbouring cell is skipped
+    // when a lower bound on the squared distance to anything assigned to it is already above
+    // the best one: it can hold neither the minimum nor an equal distance with a lower index.
     {
-      const int x0 = max(cx - 1, 0), x1 = min(cx + 1, G - 1);
-      for (int zz = max(cz - 1, 0); zz <= min(cz + 1, G - 1); ++zz)
-        for (int yy = max(cy - 1, 0); yy <= min(cy + 1, G - 1); ++yy) {
-          const int rk = base + row_key(yy, zz, g.bits);
-          scan_range(g, __ldg(g.off + rk + x0), __ldg(g.off + rk + x1 + 1), q.x, q.y, q.z, b);
+      const FaceBounds fb = face_bounds(g, q.x, q.y, q.z, cx, cy, cz);
+      int rk = base + row_key(cy, cz, g.bits);
+      scan_range(g, __ldg(g.off + rk + cx), __ldg(g.off + rk + cx + 1), q.x, q.y, q.z, b);
+      if (cx > 0 && !(fb.m[0] > b.d2)) scan_range(g, __ldg(g.off + rk + cx - 1), __ldg(g.off + rk + cx), q.x, q.y, q.z, b);
+      if (cx < G - 1 && !(fb.p[0] > b.d2))
+        scan_range(g, __ldg(g.off + rk + cx + 1), __ldg(g.off + rk + cx + 2), q.x, q.y, q.z, b);
+      // the other 8 x-rows: the 4 sharing a face with the query's row, then the 4 diagonal
+      for (int k = 0; k < 8; ++k) {
+        int dy, dz;
+        if (k < 4) {
+          dy = k < 2 ? (k & 1 ? 1 : -1) : 0;
+          dz = k < 2 ? 0 : (k & 1 ? 1 : -1);
+        } else {
+          dy = k & 1 ? 1 : -1;
+          dz = k & 2 ? 1 : -1;
         }
+        const int yy = cy + dy, zz = cz + dz;
+        if (yy < 0 || yy >= G || zz < 0 || zz >= G) continue;
+        const float lyz = (dy < 0 ? fb.m[1] : dy > 0 ? fb.p[1] : 0.f) + (dz < 0 ? fb.m[2] : dz > 0 ? fb.p[2] : 0.f);
+        if (lyz > b.d2) continue;
+        const int x0 = cx > 0 && !(lyz + fb.m[0] > b.d2) ? cx - 1 : cx;
+        const int x1 = cx < G - 1 && !(lyz + fb.p[0] > b.d2) ? cx + 1 : cx;
+        rk = base + row_key(yy, zz, g.bits);
+        scan_range(g, __ldg(g.off + rk + x0), __ldg(g.off + rk + x1 + 1), q.x, q.y, q.z, b);
+      }
     }
     int r = 1;
     bool done = b.d2 < outside_bound2(g, q.x, q.y, q.z, cx, cy, cz, 1);

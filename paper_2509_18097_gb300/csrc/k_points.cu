@@ -33,9 +33,21 @@ __global__ void k_plan(Plan* P, int bump) {
     cnt[ST_E][j] = J->E;
     cnt[ST_MOVCH][j] = (2 * G * G * G + SCAN_CHUNK - 1) / SCAN_CHUNK;
     int a = 0, t = 0, p3 = 0, cols = 0, ad = 0;
+    int aw = 0;
     for (int l = 0; l < J->L; ++l) {
-      // adjoint: a warp per row on coarse levels, per 4 rows on 128^3 and finer
-      a += J->lev[l].n >= 128 ? (*J->lev[l].n_active + 3) >> 2 : *J->lev[l].n_active;
+      // adjoint (in blocks of 8 warps): 2^adj_lg lanes per row, 8 to 16 entries per lane
+      // (a row holds one entry per point in the 8 cells around its vertex: a few dozen on
+      // fine levels, thousands on coarse ones), so a warp sums 32 >> adj_lg rows; rows of
+      // 512 entries or more on average (adj_lg = 6) get a whole block each
+      Level& lv = J->lev[l];
+      const int na = *lv.n_active;
+      const int ne = na > 0 ? lv.act_ptr[na] : 0;
+      const int avg = ne / max(na, 1);
+      int lg = 0;
+      while (lg < 6 && (16 << lg) <= avg) ++lg;
+      lv.adj_lg = lg;
+      if (lg == 6) a += na;
+      else aw += (na + (32 >> lg) - 1) >> (5 - lg);
       if (J->lev[l].n > 128) t += J->lev[l].tiles;
       else {
         p3 += J->lev[l].n;
@@ -43,7 +55,7 @@ __global__ void k_plan(Plan* P, int bump) {
         ad += (J->lev[l].n3 + 3) >> 2;
       }
     }
-    cnt[ST_ADJ][j] = a;
+    cnt[ST_ADJ][j] = a + ((aw + 7) >> 3);
     cnt[ST_TILE][j] = t;
     cnt[ST_PLANE][j] = 3 * p3;
     cnt[ST_COL][j] = cols;

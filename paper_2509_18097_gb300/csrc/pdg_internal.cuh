@@ -65,6 +65,7 @@ struct Level {
   float* ent_w;   // [8 Q] trilinear weight / L
   int* n_active;  // device scalar
   int* csum;      // scan scratch
+  int adj_lg;     // adjoint: log2 of the lanes per row, 6 = a block per row (set by the plan kernel)
 };
 
 struct Job {
