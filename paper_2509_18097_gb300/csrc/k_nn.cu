@@ -57,12 +57,12 @@ __device__ __forceinline__ float outside_bound2(const CellGrid& g, float qx, flo
   return d * d * (1.f - 4e-6f);
 }
 
-// Squared lower bounds on the distance from q to any point assigned to the cell one step
-// below (m) or above (p) the query's cell along each axis: the distance to the shared face,
-// less the same rounding margin as above, squared and shrunk by the relative rounding of a
-// squared distance.  A bound over several axes is the sum of theirs.
+// Lower bounds on the distance from q to the points assigned to other cells of its grid.
+// m[a] / p[a]: distance from q to the lower / upper face of its own cell along axis a, less
+// the same rounding margin as above (negative for a query clamped into a boundary cell).
+// A cell d steps away along a (d < 0 below) lies beyond that face plus |d| - 1 cells.
 struct FaceBounds {
-  float m[3], p[3];
+  float m[3], p[3], h[3];
 };
 
 __device__ __forceinline__ FaceBounds face_bounds(const CellGrid& g, float qx, float qy, float qz, int cx, int cy,
@@ -73,12 +73,19 @@ __device__ __forceinline__ FaceBounds face_bounds(const CellGrid& g, float qx, f
   FaceBounds f;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const float dm = fmaxf(q[a] - (g.lo[a] + (float)c[a] * g.h[a]) - margin, 0.f);
-    const float dp = fmaxf((g.lo[a] + (float)(c[a] + 1) * g.h[a]) - q[a] - margin, 0.f);
-    f.m[a] = dm * dm * (1.f - 4e-6f);
-    f.p[a] = dp * dp * (1.f - 4e-6f);
+    f.m[a] = q[a] - (g.lo[a] + (float)c[a] * g.h[a]) - margin;
+    f.p[a] = (g.lo[a] + (float)(c[a] + 1) * g.h[a]) - q[a] - margin;
+    f.h[a] = g.h[a];
   }
   return f;
+}
+
+// squared lower bound contributed by axis a for a cell d steps away (0 for d = 0), shrunk by
+// the relative rounding of a squared distance; the bound of a cell is the sum over its axes
+__device__ __forceinline__ float axis_lb(const FaceBounds& f, int a, int d) {
+  if (d == 0) return 0.f;
+  const float t = fmaxf((d < 0 ? f.m[a] : f.p[a]) + (float)(abs(d) - 1) * f.h[a], 0.f);
+  return t * t * (1.f - 4e-6f);
 }
 
 // ------------------------------------------------------------------------------ finalise
@@ -155,18 +162,28 @@ __device__ __forceinline__ void scan_range(const CellGrid& g, int s, int e, floa
 }
 
 // Candidates of row (dy, dz) of shell r around cell (cx, cy, cz): rows on the shell's
-// y/z boundary over the full x range [cx - r, cx + r], the others only at x = cx -/+ r.
+// y/z boundary over the x range [cx - r, cx + r], the others only at x = cx -/+ r.  Cells
+// whose lower bound is above min(cap, best so far) are skipped (strictly above: an equal
+// distance with a lower index must still be seen).
 __device__ __forceinline__ void scan_shell_row(const CellGrid& g, int base, int G, int cx, int cy, int cz, int r,
-                                               int dy, int dz, float qx, float qy, float qz, Best& b) {
+                                               int dy, int dz, float qx, float qy, float qz, const FaceBounds& fb,
+                                               float cap, Best& b) {
   const int yy = cy + dy, zz = cz + dz;
   if (yy < 0 || yy >= G || zz < 0 || zz >= G) return;
+  const float lim = fminf(cap, b.d2);
+  const float lyz = axis_lb(fb, 1, dy) + axis_lb(fb, 2, dz);
+  if (lyz > lim) return;
   const int rk = base + row_key(yy, zz, g.bits);
   if (max(abs(dy), abs(dz)) == r) {
-    const int x0 = max(cx - r, 0), x1 = min(cx + r, G - 1);
+    int x0 = max(cx - r, 0), x1 = min(cx + r, G - 1);
+    while (x0 < cx && lyz + axis_lb(fb, 0, x0 - cx) > lim) ++x0;
+    while (x1 > cx && lyz + axis_lb(fb, 0, x1 - cx) > lim) --x1;
     scan_range(g, __ldg(g.off + rk + x0), __ldg(g.off + rk + x1 + 1), qx, qy, qz, b);
   } else {
-    if (cx - r >= 0) scan_range(g, __ldg(g.off + rk + cx - r), __ldg(g.off + rk + cx - r + 1), qx, qy, qz, b);
-    if (cx + r < G) scan_range(g, __ldg(g.off + rk + cx + r), __ldg(g.off + rk + cx + r + 1), qx, qy, qz, b);
+    if (cx - r >= 0 && !(lyz + axis_lb(fb, 0, -r) > fminf(cap, b.d2)))
+      scan_range(g, __ldg(g.off + rk + cx - r), __ldg(g.off + rk + cx - r + 1), qx, qy, qz, b);
+    if (cx + r < G && !(lyz + axis_lb(fb, 0, r) > fminf(cap, b.d2)))
+      scan_range(g, __ldg(g.off + rk + cx + r), __ldg(g.off + rk + cx + r + 1), qx, qy, qz, b);
   }
 }
 
@@ -190,12 +207,13 @@ __global__ void __launch_bounds__(256) k_nn(const Plan* __restrict__ P) {
     // ring 1: the 3x3x3 box, the query's own cell first.  A neighbouring cell is skipped
     // when a lower bound on the squared distance to anything assigned to it is already above
     // the best one: it can hold neither the minimum nor an equal distance with a lower index.
+    const FaceBounds fb = face_bounds(g, q.x, q.y, q.z, cx, cy, cz);
     {
-      const FaceBounds fb = face_bounds(g, q.x, q.y, q.z, cx, cy, cz);
       int rk = base + row_key(cy, cz, g.bits);
       scan_range(g, __ldg(g.off + rk + cx), __ldg(g.off + rk + cx + 1), q.x, q.y, q.z, b);
-      if (cx > 0 && !(fb.m[0] > b.d2)) scan_range(g, __ldg(g.off + rk + cx - 1), __ldg(g.off + rk + cx), q.x, q.y, q.z, b);
-      if (cx < G - 1 && !(fb.p[0] > b.d2))
+      if (cx > 0 && !(axis_lb(fb, 0, -1) > b.d2))
+        scan_range(g, __ldg(g.off + rk + cx - 1), __ldg(g.off + rk + cx), q.x, q.y, q.z, b);
+      if (cx < G - 1 && !(axis_lb(fb, 0, 1) > b.d2))
         scan_range(g, __ldg(g.off + rk + cx + 1), __ldg(g.off + rk + cx + 2), q.x, q.y, q.z, b);
       // the other 8 x-rows: the 4 sharing a face with the query's row, then the 4 diagonal
       for (int k = 0; k < 8; ++k) {
@@ -209,10 +227,10 @@ __global__ void __launch_bounds__(256) k_nn(const Plan* __restrict__ P) {
         }
         const int yy = cy + dy, zz = cz + dz;
         if (yy < 0 || yy >= G || zz < 0 || zz >= G) continue;
-        const float lyz = (dy < 0 ? fb.m[1] : dy > 0 ? fb.p[1] : 0.f) + (dz < 0 ? fb.m[2] : dz > 0 ? fb.p[2] : 0.f);
+        const float lyz = axis_lb(fb, 1, dy) + axis_lb(fb, 2, dz);
         if (lyz > b.d2) continue;
-        const int x0 = cx > 0 && !(lyz + fb.m[0] > b.d2) ? cx - 1 : cx;
-        const int x1 = cx < G - 1 && !(lyz + fb.p[0] > b.d2) ? cx + 1 : cx;
+        const int x0 = cx > 0 && !(lyz + axis_lb(fb, 0, -1) > b.d2) ? cx - 1 : cx;
+        const int x1 = cx < G - 1 && !(lyz + axis_lb(fb, 0, 1) > b.d2) ? cx + 1 : cx;
         rk = base + row_key(yy, zz, g.bits);
         scan_range(g, __ldg(g.off + rk + x0), __ldg(g.off + rk + x1 + 1), q.x, q.y, q.z, b);
       }
@@ -222,7 +240,7 @@ __global__ void __launch_bounds__(256) k_nn(const Plan* __restrict__ P) {
     while (!done && r < NN_RTHREAD) {
       ++r;
       for (int dz = -r; dz <= r; ++dz)
-        for (int dy = -r; dy <= r; ++dy) scan_shell_row(g, base, G, cx, cy, cz, r, dy, dz, q.x, q.y, q.z, b);
+        for (int dy = -r; dy <= r; ++dy) scan_shell_row(g, base, G, cx, cy, cz, r, dy, dz, q.x, q.y, q.z, fb, FLT_MAX, b);
       done = b.d2 < outside_bound2(g, q.x, q.y, q.z, cx, cy, cz, r);
     }
     if (done) {
@@ -284,18 +302,20 @@ __global__ void __launch_bounds__(256) k_nn_hard(const Plan* __restrict__ P) {
     const int cx = cell_coord(q.x, g.lo[0], g.inv_h[0], G);
     const int cy = cell_coord(q.y, g.lo[1], g.inv_h[1], G);
     const int cz = cell_coord(q.z, g.lo[2], g.inv_h[2], G);
-    // continue from the thread pass: its best is lane 0's starting candidate
+    const FaceBounds fb = face_bounds(g, q.x, q.y, q.z, cx, cy, cz);
+    // continue from the thread pass: its best is lane 0's starting candidate, and the best
+    // of the warp after each ring bounds what every lane still has to look at
     Best b{FLT_MAX, 0x7fffffff};
     if (lane == 0) {
       b.d2 = __int_as_float(h.z);
       b.idx = h.w;
     }
-    Best best = b;
+    Best best{__int_as_float(h.z), h.w};
     bool done = false;
     for (int r = h.y + 1; r <= NN_RMAX && !done; ++r) {
       const int side = 2 * r + 1;
       for (int ri = lane; ri < side * side; ri += 32)
-        scan_shell_row(g, base, G, cx, cy, cz, r, ri % side - r, ri / side - r, q.x, q.y, q.z, b);
+        scan_shell_row(g, base, G, cx, cy, cz, r, ri % side - r, ri / side - r, q.x, q.y, q.z, fb, best.d2, b);
       best = warp_min(b);
       done = best.d2 < outside_bound2(g, q.x, q.y, q.z, cx, cy, cz, r);
     }
