@@ -51,7 +51,7 @@ __global__ void k_plan(Plan* P, int bump) {
       if (J->lev[l].n > 128) t += J->lev[l].tiles;
       else {
         p3 += J->lev[l].n;
-        cols += 3 * J->lev[l].n * J->lev[l].n;
+        cols += 3 * ((J->lev[l].n * J->lev[l].n + 127) / 128);  // blocks of 128 columns
         ad += (J->lev[l].n3 + 3) >> 2;
       }
     }

@@ -253,7 +253,7 @@ __device__ __forceinline__ void plane_load(float* __restrict__ plane, const floa
   const int S = n + 1;
   if (n >= 4) {
     const int nq = (n * n) >> 2;
-#pragma unroll 4
+#pragma unroll 16
     for (int i = threadIdx.x; i < nq; i += PL_THREADS) {
       const int e = i << 2, r = e >> lg, x = e & (n - 1);
       const float4 q = __ldg(reinterpret_cast<const float4*>(src + r * rstride + x));
@@ -297,109 +297,98 @@ __device__ __forceinline__ bool plane_item(const Job& J, int r, bool three, int&
   return false;
 }
 
-// The four Thomas sweeps of one column of one channel, in blocks of K steps: all loads of a
-// block are issued before its recursion runs, so the memory latency is paid once per block
-// rather than once per step.  Each channel computes the pivots of its column in its first
-// sweep (the same expression, so the same values) and keeps them in its own plane of the
-// pivot buffer, so no thread waits on another.  n is a multiple of K.
-template <int K>
-__device__ __forceinline__ void column_solve(float* __restrict__ t, float* __restrict__ rp, int n, size_t n2,
-                                             float a, float lam, float scale) {
-  float v[K], rr[K];
+// Pass B: the two tridiagonal solves T^2 h = g of one (kx, ky) column of one channel, with
+// the whole column in registers (N steps unrolled) and its reciprocal pivots in shared
+// memory.  T has diagonal b_i = a + lambda deg(i) (deg 1 at the two ends, 2 inside) and
+// off-diagonal -lambda, a = 1 + lambda (mu_kx + mu_ky).  Thomas: forward
+// r_i = 1 / (b_i + lambda c_{i-1}) with c_i = -lambda r_i, g'_i = (g_i + lambda g'_{i-1}) r_i;
+// backward h_{n-1} = g'_{n-1}, h_i = g'_i + lambda r_i h_{i+1}.  The column is read from
+// global memory once and written once (scaled by the 1/n^2 of the inverse x and y
+// transforms).  rs: this thread's pivots, stride COL_THREADS floats; volatile, so that the
+// compiler reloads them in every sweep instead of holding all N in registers beside the
+// column.  Consecutive threads take consecutive x, so every global access along z is
+// coalesced and every shared access conflict-free.
+constexpr int COL_THREADS = 128;
+
+template <int N>
+__device__ __forceinline__ void column_solve(float* __restrict__ t, volatile float* rs, float a, float lam,
+                                             float scale) {
+  constexpr int n2 = N * N;
+  float v[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) v[i] = t[i * n2];
   float cp = 0.f, g = 0.f;
-  for (int i0 = 0; i0 < n; i0 += K) {  // solve 1, forward (pivots)
 #pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = t[(i0 + k) * n2];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const int i = i0 + k;
-      const float b = a + lam * ((i == 0 || i == n - 1) ? 1.f : 2.f);
-      const float r = 1.f / (b + lam * cp);
-      rr[k] = r;
-      g = (v[k] + lam * g) * r;
-      v[k] = g;
-      cp = -lam * r;
-    }
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      t[(i0 + k) * n2] = v[k];
-      rp[(i0 + k) * n2] = rr[k];
-    }
+  for (int i = 0; i < N; ++i) {  // solve 1, forward (pivots)
+    const float b = a + lam * ((i == 0 || i == N - 1) ? 1.f : 2.f);
+    const float r = __frcp_rn(b + lam * cp);
+    rs[i * COL_THREADS] = r;
+    g = (v[i] + lam * g) * r;
+    v[i] = g;
+    cp = -lam * r;
   }
-  for (int pass = 0; pass < 3; ++pass) {  // solve 1 backward, solve 2 forward, solve 2 backward
-    const bool back = pass != 1;
-    const bool last = pass == 2;
-    if (!back) g = 0.f;
-    for (int b = 0; b < n; b += K) {
-      const int i0 = back ? n - K - b : b;
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        v[k] = t[(i0 + k) * n2];
-        rr[k] = rp[(i0 + k) * n2];
-      }
-      if (back) {
+  for (int i = N - 2; i >= 0; --i) v[i] = v[i] + lam * rs[i * COL_THREADS] * v[i + 1];  // solve 1, backward
+  g = 0.f;
 #pragma unroll
-        for (int k = K - 1; k >= 0; --k) {
-          if (i0 + k == n - 1) {  // h_{n-1} = g'_{n-1}
-            if (last) v[k] = g * scale;
-            continue;
-          }
-          g = v[k] + lam * rr[k] * g;
-          v[k] = last ? g * scale : g;
-        }
-      } else {
+  for (int i = 0; i < N; ++i) {  // solve 2, forward
+    g = (v[i] + lam * g) * rs[i * COL_THREADS];
+    v[i] = g;
+  }
+  t[(N - 1) * n2] = v[N - 1] * scale;
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-          g = (v[k] + lam * g) * rr[k];
-          v[k] = g;
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < K; ++k) t[(i0 + k) * n2] = v[k];
-    }
+  for (int i = N - 2; i >= 0; --i) {  // solve 2, backward
+    v[i] = v[i] + lam * rs[i * COL_THREADS] * v[i + 1];
+    t[i * n2] = v[i] * scale;
   }
 }
 
-// Pass B: one thread per (column, channel) of a level.  T has diagonal
-// b_i = a + lambda deg(i) (deg 1 at the two ends, 2 inside) and off-diagonal -lambda, with
-// a = 1 + lambda (mu_kx + mu_ky); the reciprocal pivots r_i = 1 / (b_i + lambda c'_{i-1})
-// (c'_i = -lambda r_i) of a column go to that channel's plane of the pivot buffer.
-// Consecutive threads take consecutive x, so every access along z is coalesced.
-__device__ __forceinline__ bool column_item(const Job& J, int r, int& l, int& col) {
+// an item is COL_THREADS consecutive columns (col = y n + x) of one channel of one level
+__device__ __forceinline__ bool column_item(const Job& J, int r, int& l, int& c, int& col0) {
   for (l = 0; l < J.L; ++l) {
     const int n = J.lev[l].n;
     if (n > 128) continue;
-    if (r < 3 * n * n) {
-      col = r;
+    const int per = (n * n + COL_THREADS - 1) / COL_THREADS;
+    if (r < 3 * per) {
+      c = r / per;
+      col0 = (r - c * per) * COL_THREADS;
       return true;
     }
-    r -= 3 * n * n;
+    r -= 3 * per;
   }
   return false;
 }
 
-__global__ void __launch_bounds__(256) k_sobz(const Plan* __restrict__ P) {
+// One block of COL_THREADS per item.
+__global__ void __launch_bounds__(COL_THREADS, 3) k_sobz(const Plan* __restrict__ P) {
+  __shared__ float rs[128 * COL_THREADS];
   const int nj = P->n_jobs;
   const int total = P->pre[ST_COL][nj];
-  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
     const int j = find_job(P->pre[ST_COL], nj, it);
     const Job& J = *P->jobs[j];
     if (!J.precondition) continue;
-    int l, cc;
-    if (!column_item(J, it - P->pre[ST_COL][j], l, cc)) continue;
+    int l, c, col0;
+    if (!column_item(J, it - P->pre[ST_COL][j], l, c, col0)) continue;
     const Level& lv = J.lev[l];
     const int n = lv.n;
-    if (n == 1) continue;  // a single vertex: T = 1
-    const size_t n2 = (size_t)n * n, n3 = lv.n3;
-    const int c = cc >> (2 * lv.lg), col = cc & (int)(n2 - 1);
+    const int col = col0 + threadIdx.x;
+    if (n == 1 || col >= n * n) continue;  // a single vertex: T = 1
     const int x = col & (n - 1), y = col >> lv.lg;
     const float lam = lv.lam;
     const float a = 1.f + lam * (__ldg(lv.mu + x) + __ldg(lv.mu + y));
-    const float scale = 1.f / (float)n2;  // the 1/n of the inverse x and y transforms
-    float* __restrict__ t = lv.tmp + (size_t)c * n3 + col;
-    float* __restrict__ rp = lv.piv + (size_t)c * n3 + col;
-    if (n >= 8) column_solve<8>(t, rp, n, n2, a, lam, scale);
-    else column_solve<1>(t, rp, n, n2, a, lam, scale);
+    const float scale = 1.f / (float)(n * n);
+    float* t = lv.tmp + (size_t)c * lv.n3 + col;
+    volatile float* r = rs + threadIdx.x;
+    switch (n) {
+      case 2: column_solve<2>(t, r, a, lam, scale); break;
+      case 4: column_solve<4>(t, r, a, lam, scale); break;
+      case 8: column_solve<8>(t, r, a, lam, scale); break;
+      case 16: column_solve<16>(t, r, a, lam, scale); break;
+      case 32: column_solve<32>(t, r, a, lam, scale); break;
+      case 64: column_solve<64>(t, r, a, lam, scale); break;
+      default: column_solve<128>(t, r, a, lam, scale); break;
+    }
   }
 }
 
@@ -572,7 +561,7 @@ void sobolev_plane_configure() {
 void launch_sobolev_plane(const Plan* P, int grid, int nmax, cudaStream_t s, int part) {
   const int smem = plane_smem_max(nmax);
   if (part < 0 || part == 0) k_sobp<0><<<grid, PL_THREADS, smem, s>>>(P);
-  if (part < 0 || part == 1) k_sobz<<<grid * 4, 256, 0, s>>>(P);
+  if (part < 0 || part == 1) k_sobz<<<grid * 3, COL_THREADS, 0, s>>>(P);
   if (part < 0 || part == 2) k_sobp_inv<<<grid, PL_THREADS, smem, s>>>(P);
   if (part < 0 || part == 3) k_adam<<<grid * 8, 256, 0, s>>>(P);
 }
