@@ -1,12 +1,11 @@
-// Grid Sobolev preconditioning (Sec. 3.2, Eq. 3) fused with Adam (Sec. 3.6) for levels of
-// up to 128^3 vertices, in three passes over shared-memory planes:
-//   A  per (z-plane, channel): DCT-II along x, then along y           g   -> tmp
-//   B  per (y-slab, channel):  for every (kx, ky) column along z, two tridiagonal solves with
-//                              T = (1 + lambda (mu_kx + mu_ky)) I + lambda L_z (T^{-2}), and the
-//                              1/n^2 of the x and y inverse transforms
-//   C  per z-plane:            inverse along y and x, then Adam on theta, m, v, channel by
-//                              channel (theta is read-modified-written per channel; its plane
-//                              stays in L2 between the three channels)
+// Grid Sobolev preconditioning (Sec. 3.2, Eq. 3) and the Adam update (Sec. 3.6) for levels
+// of up to 128^3 vertices, in four kernels:
+//   A     per (z-plane, channel), in shared memory: DCT-II along x, then along y    g   -> tmp
+//   B     per (kx, ky) column along z and channel, in registers: two tridiagonal solves with
+//         T = (1 + lambda (mu_kx + mu_ky)) I + lambda L_z (T^{-2}), and the 1/n^2 of the
+//         x and y inverse transforms                                                 tmp -> tmp
+//   C     per (z-plane, channel), in shared memory: inverse along y, then along x   tmp -> tmp
+//   Adam  elementwise on theta, m, v with the preconditioned gradient              tmp -> theta
 // Why: L_l, the free-boundary 6-neighbour Laplacian, is the Kronecker sum of three
 // path-graph Laplacians whose eigenvectors are the DCT-II basis vectors
 // cos(pi k (i + 1/2) / n) with eigenvalues mu_k = 4 sin^2(pi k / 2n).  After the x and y DCTs
