@@ -348,6 +348,7 @@ def main():
             dist.barrier()
 
     B.pdg_step(ctx, args.warmup)
+    launches_per_step = B.pdg_step_kernel_count(ctx)  # kernel nodes of the captured step graph
     B.pdg_end_frame(ctx)
     torch.cuda.synchronize()
     flush_buf = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
@@ -442,7 +443,6 @@ def main():
     if not args.no_serving:
         serving = run_serving()
 
-    launches_per_step = 18  # plan, interp, 3 scan, scatter, nn, nn_hard, iso, assemble, adjoint, 3 Sobolev, Adam, 2 loss
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import pdg_oracle as O

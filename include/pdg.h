@@ -155,6 +155,11 @@ int pdg_profile_stages(void);
 const char* pdg_profile_stage_name(int i);
 pdg_status pdg_profile_step(pdg_ctx* ctx, int n_steps, double* stage_ms, void* cuda_stream);
 
+/* Number of kernel launches one pdg_step iteration performs: the kernel nodes of the
+ * context's captured step graph, counted when the graph was captured.  *out = 0 before the
+ * first pdg_step of the context (the graph is captured then).  No GPU work. */
+pdg_status pdg_step_kernel_count(const pdg_ctx* ctx, int* out);
+
 /* Evaluates the loss and its gradients at the current grids without changing them: the
  * step's forward and backward kernels (evaluation, nearest neighbours and robust-Chamfer
  * gradient, isometry gradient, adjoint into the grids), no preconditioner, no Adam, no

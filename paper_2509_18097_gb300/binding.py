@@ -84,6 +84,7 @@ _SIGS = {
     "pdg_profile_stages": (C.c_int, []),
     "pdg_profile_stage_name": (C.c_char_p, [C.c_int]),
     "pdg_profile_step": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
+    "pdg_step_kernel_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "pdg_destroy": (None, [C.c_void_p]),
     "pdg_status_string": (C.c_char_p, [C.c_int]),
     "pdg_last_error": (C.c_char_p, [C.c_void_p]),
@@ -293,6 +294,13 @@ def pdg_profile_step(ctx, n_steps: int, stream=None) -> dict:
     buf = (C.c_double * n)()
     _check(load().pdg_profile_step(ctx, int(n_steps), buf, _stream(stream)), ctx)
     return {pdg_profile_stage_name(i): buf[i] for i in range(n)}
+
+
+def pdg_step_kernel_count(ctx) -> int:
+    """Kernel launches per pdg_step iteration (0 before the first step)."""
+    out = C.c_int(0)
+    _check(load().pdg_step_kernel_count(ctx, C.byref(out)), ctx)
+    return int(out.value)
 
 
 def pdg_destroy(ctx):

@@ -34,14 +34,24 @@ __global__ void k_plan(Plan* P, int bump) {
     cnt[ST_MOVCH][j] = (2 * G * G * G + SCAN_CHUNK - 1) / SCAN_CHUNK;
     int a = 0, t = 0, p3 = 0, cols = 0, ad = 0;
     int aw = 0;
-    for (int l = 0; l < J->L; ++l) {
+    // the levels' loads are independent: issue them level-parallel (a dependent chain of
+    // global loads per level would put a dozen memory latencies on the step's critical path)
+    const int L = J->L;
+    int na_l[MAXL], ne_l[MAXL];
+#pragma unroll
+    for (int l = 0; l < MAXL; ++l) na_l[l] = l < L ? *J->lev[l].n_active : 0;
+#pragma unroll
+    for (int l = 0; l < MAXL; ++l) ne_l[l] = na_l[l] > 0 ? J->lev[l].act_ptr[na_l[l]] : 0;
+#pragma unroll
+    for (int l = 0; l < MAXL; ++l) {
+      if (l >= L) break;
       // adjoint (in blocks of 8 warps): 2^adj_lg lanes per row, 8 to 16 entries per lane
       // (a row holds one entry per point in the 8 cells around its vertex: a few dozen on
       // fine levels, thousands on coarse ones), so a warp sums 32 >> adj_lg rows; rows of
       // 512 entries or more on average (adj_lg = 6) get a whole block each
       Level& lv = J->lev[l];
-      const int na = *lv.n_active;
-      const int ne = na > 0 ? lv.act_ptr[na] : 0;
+      const int na = na_l[l];
+      const int ne = ne_l[l];
       const int avg = ne / max(na, 1);
       int lg = 0;
       while (lg < 6 && (16 << lg) <= avg) ++lg;

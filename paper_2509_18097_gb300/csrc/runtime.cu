@@ -75,6 +75,7 @@ struct pdg_ctx {
   int nmax = 1;
   cudaStream_t cap = nullptr, cap2 = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  int graph_kernels = 0;   // kernel nodes of gexec
   std::vector<int> v2e_ptr, v2e;
 
   pdg_status fail(pdg_status s, const std::string& m) {
@@ -284,7 +285,7 @@ void launch_stage(int i, const Plan* plan, int nmax, int sms, cudaStream_t s) {
 // stages (it needs only the deformed points), the loss reduction beside the adjoint and
 // the preconditioner (nothing downstream reads it).
 pdg_status capture_step(pdg_ctx* c, const Plan* plan, int nmax, cudaStream_t cap, cudaStream_t cap2,
-                        cudaGraphExec_t* out, std::string* err, int sms) {
+                        cudaGraphExec_t* out, std::string* err, int sms, int* n_kernels = nullptr) {
   cudaGraph_t g = nullptr;
   cudaEvent_t ev[4] = {};
   for (auto& e : ev)
@@ -319,6 +320,18 @@ pdg_status capture_step(pdg_ctx* c, const Plan* plan, int nmax, cudaStream_t cap
     *err = std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e);
     if (g) cudaGraphDestroy(g);
     return PDG_ERR_CUDA;
+  }
+  if (n_kernels) {  // count the kernel nodes (what one replay launches)
+    size_t nn = 0;
+    *n_kernels = 0;
+    if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+      std::vector<cudaGraphNode_t> nodes(nn);
+      if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+        for (size_t i = 0; i < nn; ++i) {
+          cudaGraphNodeType t;
+          if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++*n_kernels;
+        }
+    }
   }
   e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
@@ -655,7 +668,7 @@ pdg_status pdg_step(pdg_ctx* c, int n_steps, void* cuda_stream) {
   if (!c->gexec) {
     // the captured launches must not start before this stream's pending set-up
     CU(c, cudaStreamSynchronize(s));
-    TRY(capture_step(c, c->dplan, c->nmax, c->cap, c->cap2, &c->gexec, &c->err, c->sms));
+    TRY(capture_step(c, c->dplan, c->nmax, c->cap, c->cap2, &c->gexec, &c->err, c->sms, &c->graph_kernels));
   }
   for (int i = 0; i < n_steps; ++i) CU(c, cudaGraphLaunch(c->gexec, s));
   c->steps_in_frame += n_steps;
@@ -665,6 +678,12 @@ pdg_status pdg_step(pdg_ctx* c, int n_steps, void* cuda_stream) {
 int pdg_profile_stages(void) { return N_STAGES; }
 
 const char* pdg_profile_stage_name(int i) { return (i >= 0 && i < N_STAGES) ? STAGE_NAMES[i] : ""; }
+
+pdg_status pdg_step_kernel_count(const pdg_ctx* c, int* out) {
+  if (!c || !out) return PDG_ERR_INVALID;
+  *out = c->gexec ? c->graph_kernels : 0;
+  return PDG_OK;
+}
 
 pdg_status pdg_profile_step(pdg_ctx* c, int n_steps, double* stage_ms, void* cuda_stream) {
   if (!c || !stage_ms || n_steps < 0) return PDG_ERR_INVALID;

@@ -67,10 +67,11 @@ def gpu_run(w, cfg_kwargs=None, thetas=None, steps=1, read=True, debug=True):
             for l, th in enumerate(thetas):
                 B.pdg_write_theta(ctx, l, np.asarray(th, np.float32).reshape(-1, 3))
         th0 = [B.pdg_read(ctx, B.BUF_THETA, l, np.empty((n**3, 3), np.float32)) for l, n in enumerate(w.res)]
+        assert B.pdg_step_kernel_count(ctx) == 0  # no step graph before the first step
         B.pdg_step(ctx, steps)
         torch.cuda.synchronize()
         V, N, M = len(w.template), len(w.source), len(w.target)
-        out = dict(theta0=th0)
+        out = dict(theta0=th0, kernels_per_step=B.pdg_step_kernel_count(ctx))
         if read:
             out["y"] = B.pdg_read(ctx, B.BUF_Y, 0, np.empty((V + N, 3), np.float32))
             out["g_pts"] = B.pdg_read(ctx, B.BUF_POINT_GRAD, 0, np.empty((V + N, 3), np.float32))

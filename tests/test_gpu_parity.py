@@ -137,3 +137,11 @@ def test_outlier_queries_use_the_ring_search():
     y = g["y"].astype(np.float64)
     H.nn_check("fwd", g["nn_fwd"], y, tgt.astype(np.float64))
     H.nn_check("rev X", g["nn_rev"][0], tgt.astype(np.float64), y[:V])
+
+
+def test_step_graph_kernel_count():
+    """One step of levels up to 128^3 is 17 launches: plan, interpolation, three scan phases
+    and the scatter of the moving grid, the two NN passes, isometry, assembly, the two loss
+    kernels, adjoint, the three preconditioner passes and Adam."""
+    g = H.gpu_run(small_sphere(seed=13), read=False)
+    assert g["kernels_per_step"] == 17
