@@ -1,6 +1,7 @@
 // Exclusive prefix sums used by the counting sorts: cell offsets of the nearest-neighbour
-// grids and row pointers of the per-level point -> vertex lists.  Three phases over
-// chunks of SCAN_CHUNK elements: chunk sums, a scan of the chunk sums, chunk scans.
+// grids and row pointers of the per-level point -> vertex lists, over chunks of SCAN_CHUNK
+// elements.  Per frame: chunk sums, a scan of the chunk sums, chunk scans.  Per step (the
+// moving grid): chunk sums, then chunk scans that add up their preceding chunk sums.
 #include "kernels.h"
 
 namespace pdg {
@@ -49,6 +50,30 @@ __device__ void chunk_sum(const int* in, int len, int chunk, int* csum) {
   int tot;
   block_excl_scan(v[0] + v[1] + v[2] + v[3], &tot);
   if (threadIdx.x == 0) csum[chunk] = tot;
+}
+
+// Exclusive scan of one chunk starting from `prefix`; `last`: also out[len] = the total.
+__device__ void chunk_scan_from(const int* in, int* out, int len, int chunk, int prefix, bool last) {
+  int v[4];
+  const int base = chunk * SCAN_CHUNK + threadIdx.x * 4;
+  load4(in, len, base, v);
+  int tot;
+  int e = block_excl_scan(v[0] + v[1] + v[2] + v[3], &tot) + prefix;
+  if (last && threadIdx.x == 0) out[len] = prefix + tot;
+  if (base + 3 < len) {
+    int4 q;
+    q.x = e; e += v[0];
+    q.y = e; e += v[1];
+    q.z = e; e += v[2];
+    q.w = e;
+    *reinterpret_cast<int4*>(out + base) = q;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (base + k < len) out[base + k] = e;
+      e += v[k];
+    }
+  }
 }
 
 __device__ void chunk_scan(const int* in, int* out, int len, int chunk, const int* csum) {
@@ -103,28 +128,34 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_mov_scan_a(const Plan* __restr
   }
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_mov_scan_b(const Plan* __restrict__ P) {
-  const int nj = P->n_jobs;
-  for (int j = blockIdx.x; j < nj; j += gridDim.x) {
-    const Job& J = *P->jobs[j];
-    const int len = mov_len(J);
-    scan_sums(J.mov.csum, (len + SCAN_CHUNK - 1) / SCAN_CHUNK, J.mov.off, len);
-  }
-}
-
+// Second phase of the moving grid's scan: every block adds up the chunk sums before its
+// own chunk itself (at most a few thousand, read from L2) instead of waiting for a separate
+// scan of the chunk sums, then scans its chunk; the last chunk also writes the total.
 __global__ void __launch_bounds__(SCAN_THREADS) k_mov_scan_c(const Plan* __restrict__ P) {
+  __shared__ int red[32];
   const int nj = P->n_jobs;
   const int total = P->pre[ST_MOVCH][nj];
   for (int it = blockIdx.x; it < total; it += gridDim.x) {
     const int j = find_job(P->pre[ST_MOVCH], nj, it);
     const Job& J = *P->jobs[j];
-    chunk_scan(J.mov.hist, J.mov.off, mov_len(J), it - P->pre[ST_MOVCH][j], J.mov.csum);
+    const int chunk = it - P->pre[ST_MOVCH][j];
+    const int len = mov_len(J);
+    const int nch = (len + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    int part = 0;
+    for (int c = threadIdx.x; c < chunk; c += SCAN_THREADS) part += __ldg(J.mov.csum + c);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    int prefix = 0;
+    for (int w = 0; w < SCAN_THREADS / 32; ++w) prefix += red[w];
+    __syncthreads();
+    chunk_scan_from(J.mov.hist, J.mov.off, len, chunk, prefix, chunk == nch - 1);
   }
 }
 
 void launch_mov_scan(const Plan* P, int grid, cudaStream_t s) {
   k_mov_scan_a<<<grid, SCAN_THREADS, 0, s>>>(P);
-  k_mov_scan_b<<<grid, SCAN_THREADS, 0, s>>>(P);
   k_mov_scan_c<<<grid, SCAN_THREADS, 0, s>>>(P);
 }
 

@@ -140,8 +140,8 @@ def test_outlier_queries_use_the_ring_search():
 
 
 def test_step_graph_kernel_count():
-    """One step of levels up to 128^3 is 17 launches: plan, interpolation, three scan phases
+    """One step of levels up to 128^3 is 16 launches: plan, interpolation, two scan phases
     and the scatter of the moving grid, the two NN passes, isometry, assembly, the two loss
     kernels, adjoint, the three preconditioner passes and Adam."""
     g = H.gpu_run(small_sphere(seed=13), read=False)
-    assert g["kernels_per_step"] == 17
+    assert g["kernels_per_step"] == 16
