@@ -104,19 +104,18 @@ class ClockSampler:
 # ------------------------------------------------------------------------------ helpers
 
 
-def candidate_flops(y, V, target, bits, lo=-1.5, hi=1.5):
+def candidate_flops(y, V, target, tbits, mbits, lo=-1.5, hi=1.5):
     """Distance evaluations of the one-ring search (8 flops each): for every query the
-    number of points in its 3x3x3 cell box, computed from the same cell grids."""
+    number of points in its 3x3x3 cell box, computed from the same cell grids (the target
+    grid for the forward queries, the moving grid for the reverse ones)."""
     import numpy as np
 
-    G = 1 << bits
-
-    def cells(p):
+    def cells(p, G):
         c = np.floor((p - lo) * (G / (hi - lo))).astype(np.int64)
         return np.clip(c, 0, G - 1)
 
-    def box_counts(pts):
-        c = cells(pts)
+    def box_counts(pts, G):
+        c = cells(pts, G)
         h = np.zeros((G + 2, G + 2, G + 2), np.int64)
         np.add.at(h, (c[:, 2] + 1, c[:, 1] + 1, c[:, 0] + 1), 1)
         b = np.zeros_like(h)
@@ -126,13 +125,13 @@ def candidate_flops(y, V, target, bits, lo=-1.5, hi=1.5):
                     b += np.roll(np.roll(np.roll(h, dz, 0), dy, 1), dx, 2)
         return b
 
-    def lookup(b, q):
-        c = cells(q)
+    def lookup(b, q, G):
+        c = cells(q, G)
         return b[c[:, 2] + 1, c[:, 1] + 1, c[:, 0] + 1].sum()
 
-    bt = box_counts(target)
-    n = lookup(bt, y)  # forward: template + source into the target
-    n += lookup(box_counts(y[:V]), target) + lookup(box_counts(y[V:]), target)
+    Gt, Gm = 1 << tbits, 1 << mbits
+    n = lookup(box_counts(target, Gt), y, Gt)  # forward: template + source into the target
+    n += lookup(box_counts(y[:V], Gm), target, Gm) + lookup(box_counts(y[V:], Gm), target, Gm)
     return 8.0 * float(n)
 
 
@@ -175,10 +174,12 @@ def max_over_ranks(value: float, dist=None, device=None) -> float:
     return float(t.item())
 
 
-def grid_bits(count):
+def grid_bits(count, per_cell=8.0):
+    """log2 cells per axis of a nearest-neighbour grid (as the library chooses it): about
+    8 points per occupied cell for the target grid, 32 for the moving grid."""
     import math
 
-    g = math.sqrt(max(count, 1) / 8.0)
+    g = math.sqrt(max(count, 1) / per_cell)
     return min(max(int(round(math.log2(max(g, 1.0)))), 2), 7)
 
 
@@ -227,7 +228,7 @@ def stage_model(stage, Q, V, M, E, res, act):
     if stage == "loss":
         return "hbm", (Q + 2 * M + E) * 4, "B"
     if stage == "mov_scan":
-        G3 = 2 * (1 << (3 * grid_bits(max(V, M))))
+        G3 = 2 * (1 << (3 * grid_bits(max(V, M), 32.0)))
         return "hbm", G3 * 8, "B"
     if stage == "mov_scatter":
         return "hbm", Q * (4 + 12 + 16), "B"
@@ -398,7 +399,7 @@ def main():
     dom = max(prof, key=prof.get)
     bound, amount, unit = stage_model(dom, Q, V, M, E, w.res, act)
     if bound == "alu":
-        amount = candidate_flops(y, V, w.target.astype(np.float64), grid_bits(M))
+        amount = candidate_flops(y, V, w.target.astype(np.float64), grid_bits(M), grid_bits(max(V, M), 32.0))
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
         achieved = amount / (prof[dom] / 1e3) / 1e12

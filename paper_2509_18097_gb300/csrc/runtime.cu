@@ -27,8 +27,10 @@ struct Arena {
   }
 };
 
-int grid_bits(long count) {
-  const double g = std::sqrt(std::max(count, 1L) / 8.0);
+// Cells per axis (log2) of a nearest-neighbour grid over `count` points on a surface, with
+// about `per_cell` points in an occupied cell.
+int grid_bits(long count, double per_cell = 8.0) {
+  const double g = std::sqrt(std::max(count, 1L) / per_cell);
   int b = (int)std::lround(std::log2(std::max(g, 1.0)));
   return std::min(std::max(b, 2), 7);
 }
@@ -179,7 +181,9 @@ Layout make_layout(const pdg_config& c, int V, int E, int max_pts) {
   L.tgt4 = a.take<float4>(max_pts);
   L.verts4 = a.take<float4>(V);
   L.tbits = grid_bits(max_pts);
-  L.mbits = grid_bits(std::max(V, max_pts));
+  // the moving grid is rebuilt every step (its offsets are a scan over all its cells):
+  // cells twice as wide as the target grid's, so the scan is 8 times shorter
+  L.mbits = grid_bits(std::max(V, max_pts), 32.0);
   const size_t tG3 = size_t(1) << (3 * L.tbits), mG3 = size_t(1) << (3 * L.mbits);
   L.t_hist = a.take<int>(tG3);
   L.t_off = a.take<int>(tG3 + 1);
