@@ -107,6 +107,7 @@ void launch_csr_build(Job* J, const Job& hJ, cudaStream_t s) {
     launch_scan_segments(&seg, 1, nullptr, nullptr, s);
     k_csr_compact<<<g2, 256, 0, s>>>(J, l);
   }
+  launch_zmask(J, hJ, s);
 }
 
 // ------------------------------------------------------------------------------ per step

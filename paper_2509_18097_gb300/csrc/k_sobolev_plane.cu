@@ -1,11 +1,11 @@
 // Grid Sobolev preconditioning (Sec. 3.2, Eq. 3) and the Adam update (Sec. 3.6) for levels
 // of up to 128^3 vertices, in four kernels:
-//   A     per (z-plane, channel), in shared memory: DCT-II along x, then along y    g   -> tmp
+//   A     per (z-plane, channel): DCT-II along x, then along y                    g   -> tmp
 //   B     per (kx, ky) column along z and channel, in registers: two tridiagonal solves with
 //         T = (1 + lambda (mu_kx + mu_ky)) I + lambda L_z (T^{-2}), and the 1/n^2 of the
-//         x and y inverse transforms                                                 tmp -> tmp
-//   C     per (z-plane, channel), in shared memory: inverse along y, then along x   tmp -> tmp
-//   Adam  elementwise on theta, m, v with the preconditioned gradient              tmp -> theta
+//         x and y inverse transforms                                                tmp -> tmp
+//   C     per (z-plane, channel): inverse along y, then along x                    tmp -> tmp
+//   Adam  elementwise on theta, m, v with the preconditioned gradient             tmp -> theta
 // Why: L_l, the free-boundary 6-neighbour Laplacian, is the Kronecker sum of three
 // path-graph Laplacians whose eigenvectors are the DCT-II basis vectors
 // cos(pi k (i + 1/2) / n) with eigenvalues mu_k = 4 sin^2(pi k / 2n).  After the x and y DCTs
@@ -16,7 +16,17 @@
 // complex sequence after the even/odd reordering that turns a DCT-II into a DFT).  The
 // length-n complex FFT is a two-stage Cooley-Tukey split n = N1 x N2 done by a group of N1
 // threads: each thread runs an N2-point DFT in registers, applies the twiddles, the group
-// transposes through padded shared memory, and each thread runs N2/N1 DFTs of N1 points.
+// transposes through a small shared scratch, and each thread runs N2/N1 DFTs of N1 points.
+// The pairing of Z_k with Z_{n-k} that separates the two packed lines is a register
+// exchange between the lanes t and N1 - t of a group.
+//
+// Data movement of A and C: the first direction reads its lines straight from global
+// memory into registers and leaves its result in a shared-memory plane; the second
+// direction reads the plane and writes straight to global memory.  The shared plane is
+// unpadded for n >= 32 with an XOR swizzle of the column index, chosen so that both access
+// shapes of the passes (4 rows x 8 consecutive columns, and 8 rows x 4 consecutive columns)
+// touch 32 distinct banks.  z-planes without an active vertex (the gradient lives on the
+// vertices near the data) are skipped by A and read as zero by B.
 #include "kernels.h"
 
 namespace pdg {
@@ -109,196 +119,234 @@ __device__ __forceinline__ void fft2(float2 (&reg)[N2], float2* sc, int t, const
 
 __device__ __forceinline__ int dsrc(int j, int n) { return j < (n >> 1) ? 2 * j : 2 * (n - 1 - j) + 1; }
 
-// Forward DCT-II (unnormalised) of lines A, B (element stride es) by a group; `act` false
-// groups take part in the synchronisation only.
+// index (frequency or position) held in output register idx of thread t after fft2
 template <int N1, int N2>
-__device__ __forceinline__ void dct2_lines(float* A, float* B, int es, float2* sc, int t, bool act,
-                                          const float2* __restrict__ twn, const float2* __restrict__ tw4) {
-  constexpr int n = N1 * N2;
-  float2 reg[N2];
-#pragma unroll
-  for (int m = 0; m < N2; ++m) {
-    const int s = dsrc(t + N1 * m, n) * es;
-    reg[m] = act ? make_float2(A[s], B[s]) : make_float2(0.f, 0.f);
-  }
-  fft2<N1, N2, false>(reg, sc, t, twn);
-#pragma unroll
-  for (int jj = 0; jj < N2 / N1; ++jj)
-#pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) sc[t + N1 * jj + N2 * k1] = reg[jj * N1 + k1];
-  __syncwarp();
-  if (act) {
-#pragma unroll
-    for (int m = 0; m < N2; ++m) {
-      const int k = t + N1 * m;
-      const float2 zk = sc[k];
-      const float2 zc = sc[(n - k) & (n - 1)];
-      // V_A = (Z_k + conj Z_{n-k}) / 2, V_B = (Z_k - conj Z_{n-k}) / 2i, X = Re(exp(-i pi k/2n) V)
-      const float2 va = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y - zc.y));
-      const float2 vb = make_float2(0.5f * (zk.y + zc.y), -0.5f * (zk.x - zc.x));
-      const float2 w = __ldg(tw4 + k);
-      A[k * es] = w.x * va.x - w.y * va.y;
-      B[k * es] = w.x * vb.x - w.y * vb.y;
-    }
-  }
-  __syncwarp();
-}
-
-// Inverse: A, B <- n C^{-1} A, n C^{-1} B (the 1/n per axis is folded into the scale).
-template <int N1, int N2>
-__device__ __forceinline__ void dct3_lines(float* A, float* B, int es, float2* sc, int t, bool act,
-                                          const float2* __restrict__ twn, const float2* __restrict__ tw4) {
-  constexpr int n = N1 * N2;
-  if (act) {
-#pragma unroll
-    for (int m = 0; m < N2; ++m) {
-      const int k = t + N1 * m;
-      const float a = A[k * es], an = k ? A[(n - k) * es] : 0.f;
-      const float b = B[k * es], bn = k ? B[(n - k) * es] : 0.f;
-      float2 w = __ldg(tw4 + k);
-      w.y = -w.y;  // exp(+i pi k / 2n);  V = w (X_k - i X_{n-k});  Z = V_A + i V_B
-      const float2 va = make_float2(w.x * a + w.y * an, w.y * a - w.x * an);
-      const float2 vb = make_float2(w.x * b + w.y * bn, w.y * b - w.x * bn);
-      sc[k] = make_float2(va.x - vb.y, va.y + vb.x);
-    }
-  }
-  __syncwarp();
-  float2 reg[N2];
-#pragma unroll
-  for (int m = 0; m < N2; ++m) reg[m] = sc[t + N1 * m];
-  __syncwarp();
-  fft2<N1, N2, true>(reg, sc, t, twn);
-  if (act) {
-#pragma unroll
-    for (int jj = 0; jj < N2 / N1; ++jj)
-#pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) {
-        const int s = dsrc(t + N1 * jj + N2 * k1, n) * es;
-        A[s] = reg[jj * N1 + k1].x;
-        B[s] = reg[jj * N1 + k1].y;
-      }
-  }
-  __syncwarp();
+__device__ __forceinline__ int out_index(int idx, int t) {
+  if (N1 == 1) return idx;
+  return t + N1 * (idx / N1) + N2 * (idx % N1);
 }
 
 constexpr int PL_THREADS = 256;
 
-__host__ __device__ constexpr int plane_n1(int n) { return n <= 16 ? 1 : (n == 32 ? 4 : (n == 64 ? 8 : (n == 128 ? 8 : 16))); }
+__host__ __device__ constexpr int plane_n1(int n) { return n <= 16 ? 1 : (n == 32 ? 4 : 8); }
 
-// Row stride of a plane in shared memory.  n + 4 keeps rows 16-byte aligned (float4 copies
-// from and to global memory) and spreads the strided line accesses of the transforms over
-// the banks: for n = 128 a warp's loads take about 1.7 times the conflict-free number of
-// shared-memory wavefronts, against 4 with a stride of n + 1.
-__host__ __device__ constexpr int plane_stride(int n) { return n >= 4 ? n + 4 : n + 1; }
-
-// shared memory of a plane pass for resolution n: plane [n][plane_stride(n)] floats +
-// per-group scratch
-int plane_smem_bytes(int n) {
-  const int N1 = plane_n1(n), N2 = n / N1;
-  const int groups = PL_THREADS / N1;
-  const int sc = N1 > 1 ? N1 * (N2 + 1) : 1;
-  return ((n * plane_stride(n) + 1) & ~1) * 4 + groups * (sc > n ? sc : n) * 8;
+// Shared plane of n x n floats: unpadded and column-swizzled for n >= 32 (the swizzle
+// keeps even/odd column pairs adjacent), row stride n + 1 below.
+template <int n>
+__device__ __forceinline__ int pidx(int r, int x) {
+  if (n >= 32) {
+    const int u = (r >> 1) & 7;
+    return r * n + (x ^ (((u & 3) << 3) | ((u >> 2) << 2)));
+  } else {
+    return r * (n + 1) + x;
+  }
 }
 
-// Transforms the lines of a plane held in shared memory.  Line l starts at plane + l * ls
-// and has element stride es.  DIR: 0 forward, 1 inverse, 2 forward + scale + inverse (scale
-// uses the z-line's (kx, ky) = (line, y) and mu of the level).
-template <int N1, int N2, int DIR>
-__device__ void plane_lines(float* plane, int ls, int es, float2* scr, const Level& lv, int y_slab) {
-  constexpr int n = N1 * N2;
-  constexpr int groups = PL_THREADS / N1;
-  const int g = threadIdx.x / N1, t = threadIdx.x % N1;
-  float2* sc = scr + g * ((N1 > 1 && N1 * (N2 + 1) > n) ? N1 * (N2 + 1) : n);
-  for (int base = 0; base < n / 2; base += groups) {
-    const int p = base + g;
-    const bool act = p < n / 2;
-    const int pl = act ? p : 0;
-    float* A = plane + (2 * pl) * ls;
-    float* B = A + ls;
-    if (DIR == 0 || DIR == 2) dct2_lines<N1, N2>(A, B, es, sc, t, act, lv.tw, lv.tw4);
-    if (DIR == 2) {
-      if (act) {
-        const float inv_n3 = 1.f / (float)lv.n3;
-        const float my = __ldg(lv.mu + y_slab);
-        const float ma = __ldg(lv.mu + 2 * pl) + my, mb = __ldg(lv.mu + 2 * pl + 1) + my;
+__host__ __device__ constexpr int plane_floats(int n) { return n >= 32 ? n * n : n * (n + 1); }
+__host__ __device__ constexpr int group_scratch(int n) {
+  return plane_n1(n) > 1 ? plane_n1(n) * (n / plane_n1(n) + 1) : 0;  // float2 per group
+}
+int scratch_bytes(int n) { return (PL_THREADS / plane_n1(n)) * group_scratch(n) * 8; }
+
+// shared memory of a plane pass for resolution n: plane + per-group FFT scratch
+int plane_smem_bytes(int n) { return ((plane_floats(n) + 1) & ~1) * 4 + scratch_bytes(n); }
+
+template <int n>
+__device__ __forceinline__ float2 plane_read2(const float* plane, int r, int x) {
+  if (n >= 32) return *reinterpret_cast<const float2*>(plane + pidx<n>(r, x));
+  return make_float2(plane[pidx<n>(r, x)], plane[pidx<n>(r, x + 1)]);
+}
+
+template <int n>
+__device__ __forceinline__ void plane_write2(float* plane, int r, int x, float2 v) {
+  if (n >= 32) {
+    *reinterpret_cast<float2*>(plane + pidx<n>(r, x)) = v;
+  } else {
+    plane[pidx<n>(r, x)] = v.x;
+    plane[pidx<n>(r, x + 1)] = v.y;
+  }
+}
+
+// Forward input of rows A, B (global, n contiguous floats each): reg[m] = (a, b) at position
+// j = t + N1 m of the even/odd reordering v[j] = x[dsrc(j)].  Each thread loads the pairs
+// (x[2s], x[2s+1]) at s = t + N1 m' (m' < N2/2): the even element is its own v[s], the odd
+// one is v[n - 1 - s] of lane t ^ (N1 - 1).
+template <int N1, int N2>
+__device__ __forceinline__ void load_fwd_rows(const float* __restrict__ rowA, const float* __restrict__ rowB, int t,
+                                              float2 (&reg)[N2]) {
+  constexpr int H = N2 / 2;
+  float2 ea[H], eb[H];
 #pragma unroll
-        for (int m = 0; m < N2; ++m) {
-          const int k = t + N1 * m;
-          const float me = __ldg(lv.mu + k);
-          const float ia = 1.f / (1.f + lv.lam * (ma + me));
-          const float ib = 1.f / (1.f + lv.lam * (mb + me));
-          A[k * es] *= ia * ia * inv_n3;
-          B[k * es] *= ib * ib * inv_n3;
-        }
-      }
-      __syncwarp();
+  for (int m = 0; m < H; ++m) {
+    ea[m] = __ldg(reinterpret_cast<const float2*>(rowA) + t + N1 * m);
+    eb[m] = __ldg(reinterpret_cast<const float2*>(rowB) + t + N1 * m);
+  }
+#pragma unroll
+  for (int m = 0; m < H; ++m) reg[m] = make_float2(ea[m].x, eb[m].x);
+#pragma unroll
+  for (int m = H; m < N2; ++m) {
+    float oa = ea[N2 - 1 - m].y, ob = eb[N2 - 1 - m].y;
+    if (N1 > 1) {
+      oa = __shfl_xor_sync(0xffffffffu, oa, N1 - 1);
+      ob = __shfl_xor_sync(0xffffffffu, ob, N1 - 1);
     }
-    if (DIR == 1 || DIR == 2) dct3_lines<N1, N2>(A, B, es, sc, t, act, lv.tw, lv.tw4);
+    reg[m] = make_float2(oa, ob);
   }
 }
 
-template <int DIR>
-__device__ void plane_lines_n(int n, float* plane, int ls, int es, float2* scr, const Level& lv, int y_slab) {
-  switch (n) {
-    case 2: plane_lines<1, 2, DIR>(plane, ls, es, scr, lv, y_slab); break;
-    case 4: plane_lines<1, 4, DIR>(plane, ls, es, scr, lv, y_slab); break;
-    case 8: plane_lines<1, 8, DIR>(plane, ls, es, scr, lv, y_slab); break;
-    case 16: plane_lines<1, 16, DIR>(plane, ls, es, scr, lv, y_slab); break;
-    case 32: plane_lines<4, 8, DIR>(plane, ls, es, scr, lv, y_slab); break;
-    case 64: plane_lines<8, 8, DIR>(plane, ls, es, scr, lv, y_slab); break;
-    case 128: plane_lines<8, 16, DIR>(plane, ls, es, scr, lv, y_slab); break;
-    default: break;
-  }
-}
-
-// Copies an n x n plane between global rows (row r at src + r * rstride, n contiguous
-// floats) and the padded shared plane, 16 bytes per access for n >= 4, with several loads
-// in flight per thread.
-__device__ __forceinline__ void plane_load(float* __restrict__ plane, const float* __restrict__ src, int n, int lg,
-                                           size_t rstride) {
-  const int S = plane_stride(n);
-  if (n >= 4) {
-    const int nq = (n * n) >> 2;
-#pragma unroll 16
-    for (int i = threadIdx.x; i < nq; i += PL_THREADS) {
-      const int e = i << 2, r = e >> lg, x = e & (n - 1);
-      *reinterpret_cast<float4*>(plane + r * S + x) = __ldg(reinterpret_cast<const float4*>(src + r * rstride + x));
+// Separates the two packed spectra after a forward fft2 and applies the DCT-II twiddle:
+// X_A[k] = Re(w_k (Z_k + conj Z_{n-k}) / 2), X_B[k] = Re(w_k (Z_k - conj Z_{n-k}) / 2i),
+// w_k = exp(-i pi k / 2n).  Z_{n-k} of lane t != 0 sits in lane N1 - t at the mirrored
+// register; lane 0 holds both ends itself.
+template <int N1, int N2>
+__device__ __forceinline__ void dct2_post(const float2 (&reg)[N2], int t, int lbase, const float2* __restrict__ tw4,
+                                          float (&XA)[N2], float (&XB)[N2]) {
+  constexpr int n = N1 * N2, J = N2 / N1;
+  const int src = lbase + ((N1 - t) & (N1 - 1));
+#pragma unroll
+  for (int idx = 0; idx < N2; ++idx) {
+    float2 zc;
+    if (N1 == 1) {
+      zc = reg[(n - idx) & (n - 1)];
+    } else {
+      const int jj = idx / N1, k1 = idx % N1;
+      const int it = (J - 1 - jj) * N1 + (N1 - 1 - k1);
+      const int i0 = jj == 0 ? ((N1 - k1) & (N1 - 1)) : (J - jj) * N1 + (N1 - 1 - k1);
+      float2 s;
+      s.x = __shfl_sync(0xffffffffu, reg[it].x, src);
+      s.y = __shfl_sync(0xffffffffu, reg[it].y, src);
+      zc = t == 0 ? reg[i0] : s;
     }
-  } else {
-    for (int e = threadIdx.x; e < n * n; e += PL_THREADS) plane[(e >> lg) * S + (e & (n - 1))] = src[(e >> lg) * rstride + (e & (n - 1))];
+    const float2 zk = reg[idx];
+    const float2 va = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y - zc.y));
+    const float2 vb = make_float2(0.5f * (zk.y + zc.y), -0.5f * (zk.x - zc.x));
+    const float2 w = __ldg(tw4 + out_index<N1, N2>(idx, t));
+    XA[idx] = w.x * va.x - w.y * va.y;
+    XB[idx] = w.x * vb.x - w.y * vb.y;
   }
 }
 
-__device__ __forceinline__ void plane_store(float* __restrict__ dst, const float* __restrict__ plane, int n, int lg,
-                                            size_t rstride) {
-  const int S = plane_stride(n);
-  if (n >= 4) {
-    const int nq = (n * n) >> 2;
-#pragma unroll 4
-    for (int i = threadIdx.x; i < nq; i += PL_THREADS) {
-      const int e = i << 2, r = e >> lg, x = e & (n - 1);
-      *reinterpret_cast<float4*>(dst + r * rstride + x) = *reinterpret_cast<const float4*>(plane + r * S + x);
+// Input of an inverse fft2 from two spectra X[m] = (X_A[k], X_B[k]), k = t + N1 m:
+// V = exp(+i pi k / 2n) (X_k - i X_{n-k}) per line (X_n = 0), Z = V_A + i V_B.
+template <int N1, int N2>
+__device__ __forceinline__ void dct3_pre(const float2 (&X)[N2], int t, int lbase, const float2* __restrict__ tw4,
+                                         float2 (&reg)[N2]) {
+  constexpr int n = N1 * N2;
+  const int src = lbase + ((N1 - t) & (N1 - 1));
+#pragma unroll
+  for (int m = 0; m < N2; ++m) {
+    float2 xn;
+    if (N1 == 1) {
+      xn = m == 0 ? make_float2(0.f, 0.f) : X[n - m];
+    } else {
+      float2 s;
+      s.x = __shfl_sync(0xffffffffu, X[N2 - 1 - m].x, src);
+      s.y = __shfl_sync(0xffffffffu, X[N2 - 1 - m].y, src);
+      const float2 own = m == 0 ? make_float2(0.f, 0.f) : X[(N2 - m) & (N2 - 1)];
+      xn = t == 0 ? own : s;
     }
-  } else {
-    for (int e = threadIdx.x; e < n * n; e += PL_THREADS) dst[(e >> lg) * rstride + (e & (n - 1))] = plane[(e >> lg) * S + (e & (n - 1))];
+    const int k = t + N1 * m;
+    float2 w = __ldg(tw4 + k);
+    w.y = -w.y;  // exp(+i pi k / 2n)
+    const float a = X[m].x, an = xn.x, b = X[m].y, bn = xn.y;
+    const float2 va = make_float2(w.x * a + w.y * an, w.y * a - w.x * an);
+    const float2 vb = make_float2(w.x * b + w.y * bn, w.y * b - w.x * bn);
+    reg[m] = make_float2(va.x - vb.y, va.y + vb.x);
   }
 }
 
-// maps a plane item of a job to (level, index); `per` items per level (3n or n), only levels
-// with 1 <= n <= 128 take part
-__device__ __forceinline__ bool plane_item(const Job& J, int r, bool three, int& l, int& idx) {
+// maps a plane item of a job to (level, index); 3n items per level (plane major, then
+// channel), only levels with n <= 128 take part
+__device__ __forceinline__ bool plane_item(const Job& J, int r, int& l, int& idx) {
   for (l = 0; l < J.L; ++l) {
     const int n = J.lev[l].n;
     if (n > 128) continue;
-    const int c = three ? 3 * n : n;
-    if (r < c) {
+    if (r < 3 * n) {
       idx = r;
       return true;
     }
-    r -= c;
+    r -= 3 * n;
   }
   return false;
 }
+
+// ------------------------------------------------------------------------------ pass A
+
+// DCT-II along x (rows, from global memory) then y (columns of the shared plane, to global
+// memory) of the z-plane `in` (n x n floats) into `out`.
+template <int N1, int N2>
+__device__ void plane_fwd(const Level& lv, const float* __restrict__ in, float* __restrict__ out, float* plane,
+                          float2* scr) {
+  constexpr int n = N1 * N2, GB = PL_THREADS / N1;
+  const int gi = threadIdx.x / N1, t = threadIdx.x % N1;
+  const int lbase = (threadIdx.x & 31) & ~(N1 - 1);
+  float2* sc = scr + gi * group_scratch(n);
+  // a group's line pairs: the condition is uniform over each warp when N1 > 1 (n N1 / 2 is a
+  // multiple of 32), and N1 = 1 has no warp-collective step
+  for (int p = gi; p < n / 2; p += GB) {  // x-lines: rows 2p, 2p + 1
+    float2 reg[N2];
+    load_fwd_rows<N1, N2>(in + (2 * p) * n, in + (2 * p + 1) * n, t, reg);
+    fft2<N1, N2, false>(reg, sc, t, lv.tw);
+    float XA[N2], XB[N2];
+    dct2_post<N1, N2>(reg, t, lbase, lv.tw4, XA, XB);
+#pragma unroll
+    for (int idx = 0; idx < N2; ++idx) {
+      const int k = out_index<N1, N2>(idx, t);
+      plane[pidx<n>(2 * p, k)] = XA[idx];
+      plane[pidx<n>(2 * p + 1, k)] = XB[idx];
+    }
+  }
+  __syncthreads();
+  for (int p = gi; p < n / 2; p += GB) {  // y-lines: columns 2p, 2p + 1
+    float2 reg[N2];
+#pragma unroll
+    for (int m = 0; m < N2; ++m) reg[m] = plane_read2<n>(plane, dsrc(t + N1 * m, n), 2 * p);
+    fft2<N1, N2, false>(reg, sc, t, lv.tw);
+    float XA[N2], XB[N2];
+    dct2_post<N1, N2>(reg, t, lbase, lv.tw4, XA, XB);
+#pragma unroll
+    for (int idx = 0; idx < N2; ++idx)
+      *reinterpret_cast<float2*>(out + out_index<N1, N2>(idx, t) * n + 2 * p) = make_float2(XA[idx], XB[idx]);
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(PL_THREADS, 2) k_sobp(const Plan* __restrict__ P) {
+  extern __shared__ float smem[];
+  const int nj = P->n_jobs;
+  const int total = P->pre[ST_PLANE][nj];
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    const int j = find_job(P->pre[ST_PLANE], nj, it);
+    const Job& J = *P->jobs[j];
+    if (!J.precondition) continue;
+    int l, idx;
+    if (!plane_item(J, it - P->pre[ST_PLANE][j], l, idx)) continue;
+    const Level& lv = J.lev[l];
+    const int n = lv.n, n3 = lv.n3;
+    const int q = idx / 3, c = idx - 3 * q;  // z-plane, channel
+    if (n == 1) {  // no transform: copy g to tmp (the scale is 1)
+      if (threadIdx.x == 0) lv.tmp[c] = lv.g[c];
+      continue;
+    }
+    // the gradient lives on the vertices near the data: a z-plane without an active vertex
+    // stays zero, and pass B reads it as zero without loading it
+    if (lv.zmask && !__ldg(lv.zmask + q)) continue;
+    const size_t off = (size_t)c * n3 + (size_t)q * n * n;
+    float* plane = smem;
+    float2* scr = reinterpret_cast<float2*>(smem + ((plane_floats(n) + 1) & ~1));
+    switch (n) {
+      case 2: plane_fwd<1, 2>(lv, lv.g + off, lv.tmp + off, plane, scr); break;
+      case 4: plane_fwd<1, 4>(lv, lv.g + off, lv.tmp + off, plane, scr); break;
+      case 8: plane_fwd<1, 8>(lv, lv.g + off, lv.tmp + off, plane, scr); break;
+      case 16: plane_fwd<1, 16>(lv, lv.g + off, lv.tmp + off, plane, scr); break;
+      case 32: plane_fwd<4, 8>(lv, lv.g + off, lv.tmp + off, plane, scr); break;
+      case 64: plane_fwd<8, 8>(lv, lv.g + off, lv.tmp + off, plane, scr); break;
+      default: plane_fwd<8, 16>(lv, lv.g + off, lv.tmp + off, plane, scr); break;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------ pass B
 
 // Pass B: the two tridiagonal solves T^2 h = g of one (kx, ky) column of one channel, with
 // the whole column in registers (N steps unrolled) and its reciprocal pivots in shared
@@ -306,7 +354,8 @@ __device__ __forceinline__ bool plane_item(const Job& J, int r, bool three, int&
 // off-diagonal -lambda, a = 1 + lambda (mu_kx + mu_ky).  Thomas: forward
 // r_i = 1 / (b_i + lambda c_{i-1}) with c_i = -lambda r_i, g'_i = (g_i + lambda g'_{i-1}) r_i;
 // backward h_{n-1} = g'_{n-1}, h_i = g'_i + lambda r_i h_{i+1}.  The column is read from
-// global memory once and written once (scaled by the 1/n^2 of the inverse x and y
+// global memory once (z-planes without an active vertex as zero, without a load) and
+// written once (scaled by the 1/n^2 of the inverse x and y
 // transforms).  rs: this thread's pivots, stride COL_THREADS floats; volatile, so that the
 // compiler reloads them in every sweep instead of holding all N in registers beside the
 // column.  Consecutive threads take consecutive x, so every global access along z is
@@ -314,12 +363,12 @@ __device__ __forceinline__ bool plane_item(const Job& J, int r, bool three, int&
 constexpr int COL_THREADS = 128;
 
 template <int N>
-__device__ __forceinline__ void column_solve(float* __restrict__ t, volatile float* rs, float a, float lam,
-                                             float scale) {
+__device__ __forceinline__ void column_solve(float* __restrict__ t, const unsigned (&zb)[4], volatile float* rs,
+                                             float a, float lam, float scale) {
   constexpr int n2 = N * N;
   float v[N];
 #pragma unroll
-  for (int i = 0; i < N; ++i) v[i] = t[i * n2];
+  for (int i = 0; i < N; ++i) v[i] = ((zb[i >> 5] >> (i & 31)) & 1u) ? t[i * n2] : 0.f;
   float cp = 0.f, g = 0.f;
 #pragma unroll
   for (int i = 0; i < N; ++i) {  // solve 1, forward (pivots)
@@ -365,6 +414,8 @@ __device__ __forceinline__ bool column_item(const Job& J, int r, int& l, int& c,
 // One block of COL_THREADS per item.
 __global__ void __launch_bounds__(COL_THREADS, 3) k_sobz(const Plan* __restrict__ P) {
   __shared__ float rs[128 * COL_THREADS];
+  __shared__ unsigned zbits[COL_THREADS / 32];
+  static_assert(COL_THREADS == 128, "one mask bit per z-plane of a 128^3 level");
   const int nj = P->n_jobs;
   const int total = P->pre[ST_COL][nj];
   for (int it = blockIdx.x; it < total; it += gridDim.x) {
@@ -375,8 +426,19 @@ __global__ void __launch_bounds__(COL_THREADS, 3) k_sobz(const Plan* __restrict_
     if (!column_item(J, it - P->pre[ST_COL][j], l, c, col0)) continue;
     const Level& lv = J.lev[l];
     const int n = lv.n;
+    if (n == 1) continue;  // a single vertex: T = 1
+    // bit i: z-plane i holds an active vertex (else it is zero and pass A did not write it);
+    // every load below is predicated on a register bit, none waits on the mask in memory
+    __syncthreads();  // the previous item has read zbits
+    {
+      const bool nz = threadIdx.x >= n || !lv.zmask || __ldg(lv.zmask + threadIdx.x);
+      const unsigned b = __ballot_sync(0xffffffffu, nz);
+      if ((threadIdx.x & 31) == 0) zbits[threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    const unsigned zb[4] = {zbits[0], zbits[1], zbits[2], zbits[3]};
     const int col = col0 + threadIdx.x;
-    if (n == 1 || col >= n * n) continue;  // a single vertex: T = 1
+    if (col >= n * n) continue;
     const int x = col & (n - 1), y = col >> lv.lg;
     const float lam = lv.lam;
     const float a = 1.f + lam * (__ldg(lv.mu + x) + __ldg(lv.mu + y));
@@ -384,68 +446,80 @@ __global__ void __launch_bounds__(COL_THREADS, 3) k_sobz(const Plan* __restrict_
     float* t = lv.tmp + (size_t)c * lv.n3 + col;
     volatile float* r = rs + threadIdx.x;
     switch (n) {
-      case 2: column_solve<2>(t, r, a, lam, scale); break;
-      case 4: column_solve<4>(t, r, a, lam, scale); break;
-      case 8: column_solve<8>(t, r, a, lam, scale); break;
-      case 16: column_solve<16>(t, r, a, lam, scale); break;
-      case 32: column_solve<32>(t, r, a, lam, scale); break;
-      case 64: column_solve<64>(t, r, a, lam, scale); break;
-      default: column_solve<128>(t, r, a, lam, scale); break;
+      case 2: column_solve<2>(t, zb, r, a, lam, scale); break;
+      case 4: column_solve<4>(t, zb, r, a, lam, scale); break;
+      case 8: column_solve<8>(t, zb, r, a, lam, scale); break;
+      case 16: column_solve<16>(t, zb, r, a, lam, scale); break;
+      case 32: column_solve<32>(t, zb, r, a, lam, scale); break;
+      case 64: column_solve<64>(t, zb, r, a, lam, scale); break;
+      default: column_solve<128>(t, zb, r, a, lam, scale); break;
     }
   }
 }
 
-// pass A: per (z-plane, channel), DCT-II along x then y
-template <int PASS>
-__global__ void __launch_bounds__(PL_THREADS, 2) k_sobp(const Plan* __restrict__ P) {
-  static_assert(PASS == 0, "the z direction is solved by k_sobp_z");
-  extern __shared__ float smem[];
-  const int nj = P->n_jobs;
-  const int total = P->pre[ST_PLANE][nj];
-  for (int it = blockIdx.x; it < total; it += gridDim.x) {
-    const int j = find_job(P->pre[ST_PLANE], nj, it);
-    const Job& J = *P->jobs[j];
-    if (!J.precondition) continue;
-    int l, idx;
-    if (!plane_item(J, it - P->pre[ST_PLANE][j], true, l, idx)) continue;
-    const Level& lv = J.lev[l];
-    const int n = lv.n, n3 = lv.n3, lg = lv.lg;
-    if (n == 1) {  // no transform: copy g to tmp (the scale is 1)
-      if (PASS == 0 && threadIdx.x == 0) lv.tmp[idx] = lv.g[idx];
-      continue;
-    }
-    const int c = idx >> lg, q = idx & (n - 1);  // channel, plane index (z for A, y for B)
-    const int S = plane_stride(n);
-    float* plane = smem;
-    float2* scr = reinterpret_cast<float2*>(smem + ((n * S + 1) & ~1));
-    // A: rows y of z-plane q (row stride n);  B: rows z of the y-slab q (row stride n^2)
-    const size_t off = (size_t)c * n3 + (PASS == 0 ? (size_t)q * n * n : (size_t)q * n);
-    const size_t rstride = PASS == 0 ? (size_t)n : (size_t)n * n;
-    plane_load(plane, (PASS == 0 ? lv.g : lv.tmp) + off, n, lg, rstride);
-    __syncthreads();
-    // the gradient lives on the vertices near the data: a plane that is all zero stays zero
-    bool any = false;
-    for (int e = threadIdx.x; e < n * n && !any; e += PL_THREADS) any = plane[(e >> lg) * S + (e & (n - 1))] != 0.f;
-    if (!__syncthreads_or(any)) {
-      plane_store(lv.tmp + off, plane, n, lg, rstride);
-      __syncthreads();
-      continue;
-    }
-    if (PASS == 0) {
-      plane_lines_n<0>(n, plane, S, 1, scr, lv, 0);  // x-lines (rows)
-      __syncthreads();
-      plane_lines_n<0>(n, plane, 1, S, scr, lv, 0);  // y-lines (columns)
-    } else {
-      plane_lines_n<2>(n, plane, 1, S, scr, lv, q);  // z-lines (columns): forward, scale, inverse
-    }
-    __syncthreads();
-    plane_store(lv.tmp + off, plane, n, lg, rstride);
-    __syncthreads();
+// ------------------------------------------------------------------------------ pass C
+
+// Inverse DCT along y (columns, from global memory) then x (rows of the shared plane) of
+// z-plane q, channel c; the preconditioned gradient goes back to tmp (coalesced pairs of
+// neighbouring columns) for the Adam kernel.
+template <int N1, int N2>
+__device__ void plane_inv(const Job& J, const Level& lv, int c, int q, float* plane, float2* scr) {
+  constexpr int n = N1 * N2, GB = PL_THREADS / N1, H = N2 / 2;
+  const int gi = threadIdx.x / N1, t = threadIdx.x % N1;
+  const int lbase = (threadIdx.x & 31) & ~(N1 - 1);
+  float2* sc = scr + gi * group_scratch(n);
+  const size_t poff = (size_t)q * n * n;
+  const float* tp = lv.tmp + (size_t)c * lv.n3 + poff;
+  for (int p = gi; p < n / 2; p += GB) {  // y-lines: columns 2p, 2p + 1
+    float2 X[N2];
+#pragma unroll
+    for (int m = 0; m < N2; ++m) X[m] = *reinterpret_cast<const float2*>(tp + (t + N1 * m) * n + 2 * p);
+    float2 reg[N2];
+    dct3_pre<N1, N2>(X, t, lbase, lv.tw4, reg);
+    fft2<N1, N2, true>(reg, sc, t, lv.tw);
+#pragma unroll
+    for (int idx = 0; idx < N2; ++idx) plane_write2<n>(plane, dsrc(out_index<N1, N2>(idx, t), n), 2 * p, reg[idx]);
   }
+  __syncthreads();
+  float* out = lv.tmp + (size_t)c * lv.n3;
+  for (int p = gi; p < n / 2; p += GB) {  // x-lines: rows 2p, 2p + 1
+    float2 X[N2];
+#pragma unroll
+    for (int m = 0; m < N2; ++m) {
+      const int k = t + N1 * m;
+      X[m] = make_float2(plane[pidx<n>(2 * p, k)], plane[pidx<n>(2 * p + 1, k)]);
+    }
+    float2 reg[N2];
+    dct3_pre<N1, N2>(X, t, lbase, lv.tw4, reg);
+    fft2<N1, N2, true>(reg, sc, t, lv.tw);
+    // z[j] is the value at x = dsrc(j): for j < n/2 the even column 2j, whose odd neighbour
+    // 2j + 1 = dsrc(n - 1 - j) sits in lane t ^ (N1 - 1) at the mirrored register
+    float2 ga[H], gb[H];
+    int xs[H];
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      const int jj = N1 == 1 ? h : h / (N1 / 2), k1 = N1 == 1 ? 0 : h % (N1 / 2);
+      const int idx = N1 == 1 ? h : jj * N1 + k1;
+      const int mir = N1 == 1 ? n - 1 - h : (N2 / N1 - 1 - jj) * N1 + (N1 - 1 - k1);
+      float2 o = reg[mir];
+      if (N1 > 1) {
+        o.x = __shfl_xor_sync(0xffffffffu, o.x, N1 - 1);
+        o.y = __shfl_xor_sync(0xffffffffu, o.y, N1 - 1);
+      }
+      xs[h] = 2 * out_index<N1, N2>(idx, t);
+      ga[h] = make_float2(reg[idx].x, o.x);
+      gb[h] = make_float2(reg[idx].y, o.y);
+    }
+    const size_t rowA = poff + (size_t)(2 * p) * n, rowB = rowA + n;
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      *reinterpret_cast<float2*>(out + rowA + xs[h]) = ga[h];
+      *reinterpret_cast<float2*>(out + rowB + xs[h]) = gb[h];
+    }
+  }
+  __syncthreads();
 }
 
-// pass C: per (z-plane, channel): inverse along y and x; the preconditioned gradient goes
-// back to tmp for the Adam kernel
 __global__ void __launch_bounds__(PL_THREADS, 2) k_sobp_inv(const Plan* __restrict__ P) {
   extern __shared__ float smem[];
   const int nj = P->n_jobs;
@@ -453,28 +527,28 @@ __global__ void __launch_bounds__(PL_THREADS, 2) k_sobp_inv(const Plan* __restri
   for (int it = blockIdx.x; it < total; it += gridDim.x) {
     const int j = find_job(P->pre[ST_PLANE], nj, it);
     const Job& J = *P->jobs[j];
+    if (!J.precondition) continue;  // the Adam kernel reads the raw gradient
     int l, idx;
-    if (!plane_item(J, it - P->pre[ST_PLANE][j], true, l, idx)) continue;
+    if (!plane_item(J, it - P->pre[ST_PLANE][j], l, idx)) continue;
     const Level& lv = J.lev[l];
-    if (!J.precondition) continue;  // Adam then reads the raw gradient
-    const int n = lv.n, n3 = lv.n3, lg = lv.lg;
-    const int c = idx >> lg, z = idx & (n - 1);
-    const int S = plane_stride(n);
+    const int n = lv.n;
+    const int q = idx / 3, c = idx - 3 * q;
+    if (n == 1) continue;  // tmp already holds the preconditioned gradient (the operator is 1)
     float* plane = smem;
-    float2* scr = reinterpret_cast<float2*>(smem + ((n * S + 1) & ~1));
-    const size_t base = (size_t)z * n * n;
-    plane_load(plane, lv.tmp + (size_t)c * n3 + base, n, lg, n);
-    __syncthreads();
-    if (n > 1) {
-      plane_lines_n<1>(n, plane, 1, S, scr, lv, 0);  // y-lines
-      __syncthreads();
-      plane_lines_n<1>(n, plane, S, 1, scr, lv, 0);  // x-lines
-      __syncthreads();
+    float2* scr = reinterpret_cast<float2*>(smem + ((plane_floats(n) + 1) & ~1));
+    switch (n) {
+      case 2: plane_inv<1, 2>(J, lv, c, q, plane, scr); break;
+      case 4: plane_inv<1, 4>(J, lv, c, q, plane, scr); break;
+      case 8: plane_inv<1, 8>(J, lv, c, q, plane, scr); break;
+      case 16: plane_inv<1, 16>(J, lv, c, q, plane, scr); break;
+      case 32: plane_inv<4, 8>(J, lv, c, q, plane, scr); break;
+      case 64: plane_inv<8, 8>(J, lv, c, q, plane, scr); break;
+      default: plane_inv<8, 16>(J, lv, c, q, plane, scr); break;
     }
-    plane_store(lv.tmp + (size_t)c * n3 + base, plane, n, lg, n);  // the preconditioned gradient
-    __syncthreads();
   }
 }
+
+// ------------------------------------------------------------------------------ Adam
 
 // Adam (PyTorch semantics) on every vertex of every level (n <= 128) from the preconditioned
 // gradient in tmp (or the raw gradient without preconditioning): 4 vertices per thread,
@@ -547,6 +621,27 @@ __global__ void __launch_bounds__(256) k_adam(const Plan* __restrict__ P) {
   }
 }
 
+// ------------------------------------------------------------------------------ per frame
+
+// zmask[z] = 1 for the z-planes of a level that hold an active vertex (per frame)
+__global__ void k_zmask(Job* __restrict__ Jp, int l) {
+  const Level& lv = Jp->lev[l];
+  const int na = *lv.n_active;
+  const int sh = 2 * lv.lg;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < na; i += gridDim.x * blockDim.x)
+    lv.zmask[lv.act_v[i] >> sh] = 1;
+}
+
+void launch_zmask(Job* J, const Job& hJ, cudaStream_t s) {
+  for (int l = 0; l < hJ.L; ++l) {
+    const Level& lv = hJ.lev[l];
+    if (!lv.zmask) continue;
+    cudaMemsetAsync(lv.zmask, 0, sizeof(int) * lv.n, s);
+    const int grid = lv.n3 / 256 + 1 < 1024 ? lv.n3 / 256 + 1 : 1024;
+    k_zmask<<<grid, 256, 0, s>>>(J, l);
+  }
+}
+
 // largest shared memory a plane pass needs over the levels n <= nmax it may meet
 int plane_smem_max(int nmax) {
   int m = 0;
@@ -556,14 +651,14 @@ int plane_smem_max(int nmax) {
 
 void sobolev_plane_configure() {
   const int smem = plane_smem_max(128);
-  cudaFuncSetAttribute(k_sobp<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_sobp, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaFuncSetAttribute(k_sobp_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 // part: 0 xy-forward, 1 z solve, 2 xy-inverse, 3 Adam, -1 all four
 void launch_sobolev_plane(const Plan* P, int grid, int nmax, cudaStream_t s, int part) {
   const int smem = plane_smem_max(nmax);
-  if (part < 0 || part == 0) k_sobp<0><<<grid, PL_THREADS, smem, s>>>(P);
+  if (part < 0 || part == 0) k_sobp<<<grid, PL_THREADS, smem, s>>>(P);
   if (part < 0 || part == 1) k_sobz<<<grid * 3, COL_THREADS, 0, s>>>(P);
   if (part < 0 || part == 2) k_sobp_inv<<<grid, PL_THREADS, smem, s>>>(P);
   if (part < 0 || part == 3) k_adam<<<grid * 8, 256, 0, s>>>(P);

@@ -17,12 +17,11 @@ namespace pdg {
 
 constexpr int STATIC_MAX_RES = PDG_STATIC_MAX_RES;
 constexpr size_t STATIC_N3 = (size_t)STATIC_MAX_RES * STATIC_MAX_RES * STATIC_MAX_RES;
-// layout: g (SoA, 3 n^3 floats) | tmp (3 n^3) | pivots (3 n^3) | mu (n) | tw (n float2) | tw4 (n float2) |
+// layout: g (SoA, 3 n^3 floats) | tmp (3 n^3) | mu (n) | tw (n float2) | tw4 (n float2) |
 //         n_active (int) + bias (2 floats, read by the pass even when it skips Adam) | job | plan
 constexpr size_t SO_G = 0;
 constexpr size_t SO_TMP = SO_G + 3 * STATIC_N3 * sizeof(float);
-constexpr size_t SO_PIV = SO_TMP + 3 * STATIC_N3 * sizeof(float);
-constexpr size_t SO_MU = SO_PIV + 3 * STATIC_N3 * sizeof(float);
+constexpr size_t SO_MU = SO_TMP + 3 * STATIC_N3 * sizeof(float);
 constexpr size_t SO_TW = SO_MU + STATIC_MAX_RES * sizeof(float);
 constexpr size_t SO_TW4 = SO_TW + STATIC_MAX_RES * sizeof(float2);
 constexpr size_t SO_NA = SO_TW4 + STATIC_MAX_RES * sizeof(float2);
@@ -104,7 +103,6 @@ extern "C" pdg_status pdg_precondition_static(int res, float lambda, const float
   lv.lam = lambda;
   lv.g = reinterpret_cast<float*>(base + SO_G);
   lv.tmp = reinterpret_cast<float*>(base + SO_TMP);
-  lv.piv = reinterpret_cast<float*>(base + SO_PIV);
   lv.mu = reinterpret_cast<float*>(base + SO_MU);
   lv.tw = reinterpret_cast<float2*>(base + SO_TW);
   lv.tw4 = reinterpret_cast<float2*>(base + SO_TW4);

@@ -51,7 +51,7 @@ struct Level {
   float* v;       // [3][n3] Adam second moment
   float* g;       // [3][n3] dLoss/dTheta (zero at vertices no point touches)
   float* tmp;     // [3][n3] spectral work array (and preconditioned gradient in debug mode)
-  float* piv;     // [3][n3] reciprocal pivots of the z-direction tridiagonal solves (n <= 128)
+  int* zmask;     // [n] 1 for z-planes that hold an active vertex (per frame); null: all planes
   float* mu;      // [n] eigenvalues 4 sin^2(pi k / 2n) of the 1-D path Laplacian
   float2* tw;     // [n] FFT twiddles exp(-2 pi i k / n)
   float2* tw4;    // [n] DCT twiddles exp(-i pi k / 2n)

@@ -118,7 +118,7 @@ struct Layout {
   size_t total = 0;
   size_t job, plan, flag, stage, op_job, op_plan;
   struct Lv {
-    size_t theta, m, v, g, tmp, piv, mu, tw, tw4, cnt, rowptr, flag, act_v, act_ptr, ent_p, ent_w, n_active, csum;
+    size_t theta, m, v, g, tmp, zmask, mu, tw, tw4, cnt, rowptr, flag, act_v, act_ptr, ent_p, ent_w, n_active, csum;
     int cap;
   } lv[MAXL];
   size_t x, y, gfwd, gy, acc, loss_fwd, loss_rev, loss_iso, nn_fwd, nn_rev, edge_d, edges, e_prev, v2e_ptr, v2e;
@@ -148,7 +148,7 @@ Layout make_layout(const pdg_config& c, int V, int E, int max_pts) {
     v.v = a.take<float>(3 * n3);
     v.g = a.take<float>(3 * n3);
     v.tmp = a.take<float>(3 * n3);
-    v.piv = a.take<float>(n <= 128 ? 3 * n3 : 1);
+    v.zmask = a.take<int>(n);
     v.mu = a.take<float>(n);
     v.tw = a.take<float2>(n);
     v.tw4 = a.take<float2>(n);
@@ -521,7 +521,7 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
     lv.v = (float*)P(o.v);
     lv.g = (float*)P(o.g);
     lv.tmp = (float*)P(o.tmp);
-    lv.piv = (float*)P(o.piv);
+    lv.zmask = (int*)P(o.zmask);
     lv.mu = (float*)P(o.mu);
     lv.tw = (float2*)P(o.tw);
     lv.tw4 = (float2*)P(o.tw4);
@@ -890,6 +890,7 @@ pdg_status pdg_precondition(pdg_ctx* c, int level, const float* g, float* out, v
   Job oj = c->h;
   oj.L = 1;
   oj.lev[0] = lv;
+  oj.lev[0].zmask = nullptr;  // a caller's gradient may be non-zero on any plane
   oj.precondition = 1;
   oj.keep_pgrad = 1;
   oj.no_adam = 1;
