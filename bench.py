@@ -139,7 +139,7 @@ def candidate_flops(y, V, target, tbits, mbits, lo=-1.5, hi=1.5):
 STAGE_KERNEL = {
     "interp": ("k_interp", "k_points.cu"), "mov_scatter": ("k_mov_scatter", "k_points.cu"),
     "nn": ("k_nn", "k_nn.cu"), "nn_hard": ("k_nn_hard", "k_nn.cu"), "adjoint": ("k_adjoint", "k_adjoint.cu"),
-    "sob_xy_fwd": ("k_sobp<0>", "k_sobolev_plane.cu"), "sob_z": ("k_sobz", "k_sobolev_plane.cu"),
+    "sob_xy_fwd": ("k_sobp", "k_sobolev_plane.cu"), "sob_z": ("k_sobz", "k_sobolev_plane.cu"),
     "sob_xy_inv": ("k_sobp_inv", "k_sobolev_plane.cu"), "adam": ("k_adam", "k_sobolev_plane.cu"),
     "iso_edges": ("k_iso_edges", "k_points.cu"),
     "assemble": ("k_assemble", "k_points.cu"),

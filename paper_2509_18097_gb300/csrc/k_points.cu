@@ -7,26 +7,29 @@ namespace pdg {
 
 // ------------------------------------------------------------------------------ plan
 
-// Computes, on the device, the per-stage item prefixes over the jobs of a plan.  bump = 1:
-// a new optimisation step (advances each job's Adam step count and its bias corrections
+// Start of a step for one job, done by the thread of the job's first point in k_interp.
+// bump = 1: a new optimisation step (advances the Adam step count and its bias corrections
 // and clears the per-step counters); bump = 2: an evaluation (clears the counters only).
-// One block.
-__global__ void k_plan(Plan* P, int bump) {
+__device__ __forceinline__ void job_bump(const Job& J, int bump) {
+  *J.hard_count = 0;
+  *J.gmax = 0u;
+  if (bump == 1) {
+    const int k = *J.step + 1;
+    *J.step = k;
+    // 1 - beta^k = -expm1(k log1p(beta - 1)): no cancellation for small k (beta - 1 is exact)
+    J.bias[0] = 1.f / -expm1f((float)k * log1pf(J.beta1 - 1.f));
+    J.bias[1] = rsqrtf(-expm1f((float)k * log1pf(J.beta2 - 1.f)));
+  }
+}
+
+// Computes, on the device, the per-stage item prefixes over the jobs of a plan.  They change
+// only when a job starts a frame (its active-vertex counts) or the membership changes, so
+// the host launches this outside the per-step graph, when the plan is stale.  One block.
+__global__ void k_plan(Plan* P) {
   __shared__ int cnt[NSTAGE][MAXJ];
   const int nj = P->n_jobs;
   for (int j = threadIdx.x; j < nj; j += blockDim.x) {
     Job* J = P->jobs[j];
-    if (bump) {
-      *J->hard_count = 0;
-      *J->gmax = 0u;
-    }
-    if (bump == 1) {
-      int k = *J->step + 1;
-      *J->step = k;
-      // 1 - beta^k = -expm1(k log1p(beta - 1)): no cancellation for small k (beta - 1 is exact)
-      J->bias[0] = 1.f / -expm1f((float)k * log1pf(J->beta1 - 1.f));
-      J->bias[1] = rsqrtf(-expm1f((float)k * log1pf(J->beta2 - 1.f)));
-    }
     const int G = 1 << J->mov.bits;
     cnt[ST_Q][j] = J->Q;
     cnt[ST_NNQ][j] = J->Q + 2 * J->M;
@@ -87,50 +90,75 @@ __global__ void k_plan(Plan* P, int bump) {
 
 // ------------------------------------------------------------------------------ (a) eval
 
-// u(p) = (1/L) sum_l sum_{8 corners} w * theta_l[corner]   (Eq. 1; vertex-aligned levels,
-// coordinates clamped to the domain, last cell closed)
+// The 8 corner values of a point in one level and its fractional coordinates (Eq. 1;
+// vertex-aligned levels, coordinates clamped to the domain, last cell closed).  A level of
+// one vertex has the constant value c[0].
+struct LevelTap {
+  float4 c[8];
+  float fx, fy, fz;
+  bool one;
+};
+
+__device__ __forceinline__ void level_tap(const Job& J, const Level& lv, float px, float py, float pz, LevelTap& T) {
+  const int n = lv.n;
+  T.one = n == 1;
+  if (T.one) {
+    T.c[0] = lv.theta[0];
+    T.fx = T.fy = T.fz = 0.f;
+    return;
+  }
+  int ix, iy, iz;
+  grid_coord(px, J.lo[0], lv.sc_hi[0], lv.sc_lo[0], n, ix, T.fx);
+  grid_coord(py, J.lo[1], lv.sc_hi[1], lv.sc_lo[1], n, iy, T.fy);
+  grid_coord(pz, J.lo[2], lv.sc_hi[2], lv.sc_lo[2], n, iz, T.fz);
+  const float4* t0 = lv.theta + ((size_t)(iz * n + iy) * n + ix);
+  const float4* t1 = t0 + (size_t)n * n;
+  T.c[0] = t0[0]; T.c[1] = t0[1]; T.c[2] = t0[n]; T.c[3] = t0[n + 1];
+  T.c[4] = t1[0]; T.c[5] = t1[1]; T.c[6] = t1[n]; T.c[7] = t1[n + 1];
+}
+
+__device__ __forceinline__ void level_add(const LevelTap& T, float& ux, float& uy, float& uz) {
+  if (T.one) {
+    ux += T.c[0].x; uy += T.c[0].y; uz += T.c[0].z;
+    return;
+  }
+  const float fx = T.fx, fy = T.fy, fz = T.fz;
+  const float4 c000 = T.c[0], c100 = T.c[1], c010 = T.c[2], c110 = T.c[3];
+  const float4 c001 = T.c[4], c101 = T.c[5], c011 = T.c[6], c111 = T.c[7];
+  const float gx = 1.f - fx, gy = 1.f - fy, gz = 1.f - fz;
+  const float w000 = gx * gy * gz, w100 = fx * gy * gz, w010 = gx * fy * gz, w110 = fx * fy * gz;
+  const float w001 = gx * gy * fz, w101 = fx * gy * fz, w011 = gx * fy * fz, w111 = fx * fy * fz;
+  ux += w000 * c000.x + w100 * c100.x + w010 * c010.x + w110 * c110.x + w001 * c001.x + w101 * c101.x +
+        w011 * c011.x + w111 * c111.x;
+  uy += w000 * c000.y + w100 * c100.y + w010 * c010.y + w110 * c110.y + w001 * c001.y + w101 * c101.y +
+        w011 * c011.y + w111 * c111.y;
+  uz += w000 * c000.z + w100 * c100.z + w010 * c010.z + w110 * c110.z + w001 * c001.z + w101 * c101.z +
+        w011 * c011.z + w111 * c111.z;
+}
+
+// u(p) = (1/L) sum_l sum_{8 corners} w * theta_l[corner]   (Eq. 1), levels summed in order
 __device__ float3 eval_disp(const Job& J, float px, float py, float pz) {
   float ux = 0.f, uy = 0.f, uz = 0.f;
   for (int l = 0; l < J.L; ++l) {
-    const Level& lv = J.lev[l];
-    const int n = lv.n;
-    if (n == 1) {
-      const float4 t = lv.theta[0];
-      ux += t.x; uy += t.y; uz += t.z;
-      continue;
-    }
-    int ix, iy, iz;
-    float fx, fy, fz;
-    grid_coord(px, J.lo[0], lv.sc_hi[0], lv.sc_lo[0], n, ix, fx);
-    grid_coord(py, J.lo[1], lv.sc_hi[1], lv.sc_lo[1], n, iy, fy);
-    grid_coord(pz, J.lo[2], lv.sc_hi[2], lv.sc_lo[2], n, iz, fz);
-    const float4* t0 = lv.theta + ((size_t)(iz * n + iy) * n + ix);
-    const float4* t1 = t0 + (size_t)n * n;
-    const float4 c000 = t0[0], c100 = t0[1], c010 = t0[n], c110 = t0[n + 1];
-    const float4 c001 = t1[0], c101 = t1[1], c011 = t1[n], c111 = t1[n + 1];
-    const float gx = 1.f - fx, gy = 1.f - fy, gz = 1.f - fz;
-    const float w000 = gx * gy * gz, w100 = fx * gy * gz, w010 = gx * fy * gz, w110 = fx * fy * gz;
-    const float w001 = gx * gy * fz, w101 = fx * gy * fz, w011 = gx * fy * fz, w111 = fx * fy * fz;
-    ux += w000 * c000.x + w100 * c100.x + w010 * c010.x + w110 * c110.x + w001 * c001.x + w101 * c101.x +
-          w011 * c011.x + w111 * c111.x;
-    uy += w000 * c000.y + w100 * c100.y + w010 * c010.y + w110 * c110.y + w001 * c001.y + w101 * c101.y +
-          w011 * c011.y + w111 * c111.y;
-    uz += w000 * c000.z + w100 * c100.z + w010 * c010.z + w110 * c110.z + w001 * c001.z + w101 * c101.z +
-          w011 * c011.z + w111 * c111.z;
+    LevelTap A;
+    level_tap(J, J.lev[l], px, py, pz, A);
+    level_add(A, ux, uy, uz);
   }
   const float invL = 1.f / (float)J.L;
   return make_float3(ux * invL, uy * invL, uz * invL);
 }
 
 // y = x + u(x) on Q; the cell key of y in the moving grid (set 0: template, set 1: source)
-// and its count; clears the point's fixed-point reverse-Chamfer accumulator.
-__global__ void k_interp(const Plan* __restrict__ P) {
+// and its count; clears the point's fixed-point reverse-Chamfer accumulator.  The thread of
+// a job's first point also starts the job's step (job_bump; bump 0: none).
+__global__ void k_interp(const Plan* __restrict__ P, int bump) {
   const int nj = P->n_jobs;
   const int total = P->pre[ST_Q][nj];
   for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
     const int j = find_job(P->pre[ST_Q], nj, it);
     const Job& J = *P->jobs[j];
     const int p = it - P->pre[ST_Q][j];
+    if (bump && p == 0) job_bump(J, bump);
     const float4 x = J.x[p];
     const float3 u = eval_disp(J, x.x, x.y, x.z);
     const float4 y = make_float4(x.x + u.x, x.y + u.y, x.z + u.z, 0.f);
@@ -378,8 +406,8 @@ __global__ void k_deform(const Job* __restrict__ J, const float* __restrict__ in
 
 static inline int blocks_for(int n, int threads) { return max(1, min((n + threads - 1) / threads, 4096)); }
 
-void launch_plan(Plan* P, int bump, cudaStream_t s) { k_plan<<<1, 256, 0, s>>>(P, bump); }
-void launch_interp(const Plan* P, int grid, cudaStream_t s) { k_interp<<<grid, 256, 0, s>>>(P); }
+void launch_plan(Plan* P, cudaStream_t s) { k_plan<<<1, 256, 0, s>>>(P); }
+void launch_interp(const Plan* P, int grid, cudaStream_t s, int bump) { k_interp<<<grid, 256, 0, s>>>(P, bump); }
 void launch_mov_scatter(const Plan* P, int grid, cudaStream_t s) { k_mov_scatter<<<grid, 256, 0, s>>>(P); }
 void launch_iso_edges(const Plan* P, int grid, cudaStream_t s) { k_iso_edges<<<grid, 256, 0, s>>>(P); }
 void launch_assemble(const Plan* P, int grid, cudaStream_t s) { k_assemble<<<grid, 256, 0, s>>>(P); }

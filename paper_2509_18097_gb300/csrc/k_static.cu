@@ -139,7 +139,7 @@ extern "C" pdg_status pdg_precondition_static(int res, float lambda, const float
     return PDG_ERR_CUDA;
   const Plan* dP = reinterpret_cast<const Plan*>(base + SO_PLAN);
   launch_aos_to_soa(g, lv.g, n3, s);
-  launch_plan(const_cast<Plan*>(dP), 0, s);
+  launch_plan(const_cast<Plan*>(dP), s);
   int sms = 1, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -5,8 +5,8 @@
 namespace pdg {
 
 // per step (plan-driven; `grid` = blocks of the persistent launch)
-void launch_plan(Plan* P, int bump, cudaStream_t s);
-void launch_interp(const Plan* P, int grid, cudaStream_t s);
+void launch_plan(Plan* P, cudaStream_t s);
+void launch_interp(const Plan* P, int grid, cudaStream_t s, int bump);
 void launch_mov_scan(const Plan* P, int grid, cudaStream_t s);
 void launch_mov_scatter(const Plan* P, int grid, cudaStream_t s);
 void launch_nn(const Plan* P, int grid, cudaStream_t s);

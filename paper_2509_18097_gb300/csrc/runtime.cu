@@ -78,6 +78,8 @@ struct pdg_ctx {
   cudaStream_t cap = nullptr, cap2 = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int graph_kernels = 0;   // kernel nodes of gexec
+  bool plan_stale = true;  // dplan's item prefixes predate the current frame
+  unsigned long long frame_gen = 0;  // frames begun (a batch recomputes its plan when one changes)
   std::vector<int> v2e_ptr, v2e;
 
   pdg_status fail(pdg_status s, const std::string& m) {
@@ -97,6 +99,7 @@ struct pdg_batch {
   std::vector<pdg_ctx*> members;
   Plan* dplan = nullptr;
   Plan* hplan = nullptr;  // pinned host copy
+  std::vector<unsigned long long> gens;  // members' frame_gen when dplan's prefixes were computed
   cudaStream_t cap = nullptr, cap2 = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int graph_nmax = 0;
@@ -250,40 +253,42 @@ pdg_status upload_job(pdg_ctx* c, cudaStream_t s) {
 
 // The step as an explicit list of stages; the graph capture and the profiling path launch
 // exactly the same sequence.
-const char* const STAGE_NAMES[] = {"plan",      "interp",    "mov_scan",    "mov_scatter",    "nn",
-                                   "nn_hard",   "iso_edges", "assemble",    "adjoint",        "sob_xy_fwd",
-                                   "sob_z",     "sob_xy_inv", "adam",     "sobolev_256",    "loss"};
+const char* const STAGE_NAMES[] = {"interp",     "mov_scan", "mov_scatter", "nn",          "nn_hard",
+                                   "iso_edges",  "assemble", "adjoint",     "sob_xy_fwd",  "sob_z",
+                                   "sob_xy_inv", "adam",     "sobolev_256", "loss"};
 constexpr int N_STAGES = sizeof(STAGE_NAMES) / sizeof(STAGE_NAMES[0]);
 
-void launch_stage(int i, const Plan* plan, int nmax, int sms, cudaStream_t s) {
+// Stage i of a step; bump: the job_bump mode of the interpolation stage (1: optimisation
+// step, 2: evaluation).  The plan's item prefixes must be current (refresh_plan).
+void launch_stage(int i, const Plan* plan, int nmax, int sms, cudaStream_t s, int bump = 1) {
   const int grid = sms * 8;
   const int smem = sobolev_smem_bytes(nmax);
   const int tiles_per_sm = std::max(1, std::min(4, (227 * 1024) / std::max(smem, 1)));
   switch (i) {
-    case 0: launch_plan(const_cast<Plan*>(plan), 1, s); break;
-    case 1: launch_interp(plan, grid, s); break;
-    case 2: launch_mov_scan(plan, sms * 2, s); break;
-    case 3: launch_mov_scatter(plan, grid, s); break;
-    case 4: launch_nn(plan, grid, s); break;
-    case 5: launch_nn_hard(plan, sms * 4, s); break;
-    case 6: launch_iso_edges(plan, grid, s); break;
-    case 7: launch_assemble(plan, grid, s); break;
-    case 8: launch_adjoint(plan, grid, s); break;
+    case 0: launch_interp(plan, grid, s, bump); break;
+    case 1: launch_mov_scan(plan, sms * 2, s); break;
+    case 2: launch_mov_scatter(plan, grid, s); break;
+    case 3: launch_nn(plan, grid, s); break;
+    case 4: launch_nn_hard(plan, sms * 4, s); break;
+    case 5: launch_iso_edges(plan, grid, s); break;
+    case 6: launch_assemble(plan, grid, s); break;
+    case 7: launch_adjoint(plan, grid, s); break;
+    case 8:
     case 9:
     case 10:
-    case 11:
-    case 12: {
+    case 11: {
       const int ps = plane_smem_max(nmax);
       const int per_sm = std::max(1, std::min(8, (227 * 1024) / ps));
-      launch_sobolev_plane(plan, sms * per_sm, nmax, s, i - 9);
+      launch_sobolev_plane(plan, sms * per_sm, nmax, s, i - 8);
       break;
     }
-    case 13:
+    case 12:
       if (nmax > 128) launch_sobolev_tiles(plan, sms * tiles_per_sm, nmax, s);
       break;
-    case 14: launch_loss(plan, sms * 2, s); break;
+    case 13: launch_loss(plan, sms * 2, s); break;
   }
 }
+constexpr int ST_SOB_FIRST = 8, ST_SOB_LAST = 12;  // preconditioner and Adam stages
 
 // Captures one step.  Two branches: the isometry kernel runs beside the nearest-neighbour
 // stages (it needs only the deformed points), the loss reduction beside the adjoint and
@@ -303,20 +308,19 @@ pdg_status capture_step(pdg_ctx* c, const Plan* plan, int nmax, cudaStream_t cap
     for (auto& x : ev) cudaEventDestroy(x);
     return PDG_ERR_CUDA;
   }
-  launch_stage(0, plan, nmax, sms, cap);  // plan
-  launch_stage(1, plan, nmax, sms, cap);  // interp
+  launch_stage(0, plan, nmax, sms, cap);  // interp (starts the step of every job)
   cudaEventRecord(ev[0], cap);
   cudaStreamWaitEvent(cap2, ev[0], 0);
-  launch_stage(6, plan, nmax, sms, cap2);  // iso_edges
+  launch_stage(5, plan, nmax, sms, cap2);  // iso_edges
   cudaEventRecord(ev[1], cap2);
-  for (int i = 2; i <= 5; ++i) launch_stage(i, plan, nmax, sms, cap);  // moving grid, NN
+  for (int i = 1; i <= 4; ++i) launch_stage(i, plan, nmax, sms, cap);  // moving grid, NN
   cudaStreamWaitEvent(cap, ev[1], 0);
-  launch_stage(7, plan, nmax, sms, cap);  // assemble
+  launch_stage(6, plan, nmax, sms, cap);  // assemble
   cudaEventRecord(ev[2], cap);
   cudaStreamWaitEvent(cap2, ev[2], 0);
-  launch_stage(14, plan, nmax, sms, cap2);  // loss
+  launch_stage(13, plan, nmax, sms, cap2);  // loss
   cudaEventRecord(ev[3], cap2);
-  for (int i = 8; i <= 13; ++i) launch_stage(i, plan, nmax, sms, cap);  // adjoint, preconditioner, Adam
+  for (int i = 7; i <= 12; ++i) launch_stage(i, plan, nmax, sms, cap);  // adjoint, preconditioner, Adam
   cudaStreamWaitEvent(cap, ev[3], 0);
   e = cudaStreamEndCapture(cap, &g);
   for (auto& x : ev) cudaEventDestroy(x);
@@ -634,6 +638,15 @@ pdg_status pdg_set_debug(pdg_ctx* c, int keep_pgrad) {
   return upload_job(c, 0) == PDG_OK ? c->cuda(cudaDeviceSynchronize(), "set_debug") : PDG_ERR_CUDA;
 }
 
+// Recomputes the context's plan prefixes (stream-ordered) if a frame began since the last time.
+pdg_status refresh_plan(pdg_ctx* c, cudaStream_t s) {
+  if (!c->plan_stale) return PDG_OK;
+  launch_plan(c->dplan, s);
+  CU(c, cudaGetLastError());
+  c->plan_stale = false;
+  return PDG_OK;
+}
+
 pdg_status pdg_begin_frame(pdg_ctx* c, const float* target_xyz, int n_tgt, void* cuda_stream) {
   if (!c) return PDG_ERR_INVALID;
   if (c->in_frame) return c->fail(PDG_ERR_STATE, "a frame is already open");
@@ -661,6 +674,8 @@ pdg_status pdg_begin_frame(pdg_ctx* c, const float* target_xyz, int n_tgt, void*
   CU(c, cudaGetLastError());
   c->in_frame = true;
   c->steps_in_frame = 0;
+  c->plan_stale = true;
+  ++c->frame_gen;
   return PDG_OK;
 }
 
@@ -674,6 +689,7 @@ pdg_status pdg_step(pdg_ctx* c, int n_steps, void* cuda_stream) {
     CU(c, cudaStreamSynchronize(s));
     TRY(capture_step(c, c->dplan, c->nmax, c->cap, c->cap2, &c->gexec, &c->err, c->sms, &c->graph_kernels));
   }
+  TRY(refresh_plan(c, s));
   for (int i = 0; i < n_steps; ++i) CU(c, cudaGraphLaunch(c->gexec, s));
   c->steps_in_frame += n_steps;
   return PDG_OK;
@@ -696,7 +712,7 @@ pdg_status pdg_profile_step(pdg_ctx* c, int n_steps, double* stage_ms, void* cud
   cudaEvent_t ev[N_STAGES + 1];
   for (auto& e : ev) CU(c, cudaEventCreate(&e));
   for (int i = 0; i < N_STAGES; ++i) stage_ms[i] = 0.0;
-  pdg_status st = PDG_OK;
+  pdg_status st = refresh_plan(c, s);
   for (int k = 0; k < n_steps && st == PDG_OK; ++k) {
     for (int i = 0; i < N_STAGES; ++i) {
       cudaEventRecord(ev[i], s);
@@ -864,9 +880,9 @@ pdg_status pdg_eval(pdg_ctx* c, double* loss, void* cuda_stream) {
   if (!c) return PDG_ERR_INVALID;
   if (!c->in_frame) return c->fail(PDG_ERR_STATE, "pdg_eval outside a frame");
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  launch_plan(c->dplan, 2, s);
-  for (int i = 1; i < N_STAGES; ++i)
-    if (i < 9 || i > 13) launch_stage(i, c->dplan, c->nmax, c->sms, s);  // no preconditioner, no Adam
+  TRY(refresh_plan(c, s));
+  for (int i = 0; i < N_STAGES; ++i)  // no preconditioner, no Adam, no step count
+    if (i < ST_SOB_FIRST || i > ST_SOB_LAST) launch_stage(i, c->dplan, c->nmax, c->sms, s, 2);
   CU(c, cudaGetLastError());
   if (loss) {
     CU(c, cudaMemcpyAsync(loss, c->h.loss, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -900,8 +916,8 @@ pdg_status pdg_precondition(pdg_ctx* c, int level, const float* g, float* out, v
   op.jobs[0] = c->op_job;
   CU(c, cudaMemcpyAsync(c->op_job, &oj, sizeof(Job), cudaMemcpyHostToDevice, s));
   CU(c, cudaMemcpyAsync(c->op_plan, &op, sizeof(Plan), cudaMemcpyHostToDevice, s));
-  launch_plan(c->op_plan, 0, s);
-  for (int i = 9; i <= 13; ++i) launch_stage(i, c->op_plan, lv.n, c->sms, s);
+  launch_plan(c->op_plan, s);
+  for (int i = ST_SOB_FIRST; i <= ST_SOB_LAST; ++i) launch_stage(i, c->op_plan, lv.n, c->sms, s);
   launch_soa_to_aos(lv.tmp, tmp, lv.n3, s);
   CU(c, cudaGetLastError());
   const pdg_status st = copy_out(c, out, tmp, bytes, s);
@@ -979,6 +995,16 @@ pdg_status pdg_batch_step(pdg_batch* b, int n_steps, void* cuda_stream) {
     if (cudaMemcpyAsync(b->dplan, b->hplan, sizeof(Plan), cudaMemcpyHostToDevice, s) != cudaSuccess)
       return PDG_ERR_CUDA;
     b->dirty = false;
+    b->gens.clear();
+  }
+  // item prefixes: recomputed when the membership changed or a member began a frame
+  bool stale = b->gens.size() != b->members.size();
+  for (size_t i = 0; i < b->members.size() && !stale; ++i) stale = b->gens[i] != b->members[i]->frame_gen;
+  if (stale) {
+    launch_plan(b->dplan, s);
+    if (cudaGetLastError() != cudaSuccess) return PDG_ERR_CUDA;
+    b->gens.resize(b->members.size());
+    for (size_t i = 0; i < b->members.size(); ++i) b->gens[i] = b->members[i]->frame_gen;
   }
   if (!b->gexec || nmax > b->graph_nmax) {
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
