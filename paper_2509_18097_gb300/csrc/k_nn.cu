@@ -204,6 +204,20 @@ __global__ void __launch_bounds__(256) k_nn(const Plan* __restrict__ P) {
     const int cy = cell_coord(q.y, g.lo[1], g.inv_h[1], G);
     const int cz = cell_coord(q.z, g.lo[2], g.inv_h[2], G);
     Best b{FLT_MAX, 0x7fffffff};
+    // warm start: the query's neighbour of the previous step (of this frame), at its current
+    // position, compared with the same expression as every other candidate.  It is one of
+    // the set's points, so the search below, which skips only cells that cannot hold a
+    // distance <= the best, still ends at the exact lexicographic minimum; starting close to
+    // it lets that pruning work from the first cell.
+    {
+      const int w = q.fwd ? J.nn_fwd[q.id] : J.nn_rev[q.set * J.M + q.id];
+      if (w >= 0) {
+        const int gid = q.fwd ? w : w + (q.set ? J.V : 0);
+        const float4 p = q.fwd ? J.tgt4[w] : J.y[gid];
+        b.d2 = sqdist(q.x, q.y, q.z, p.x, p.y, p.z);
+        b.idx = gid;
+      }
+    }
     // ring 1: the 3x3x3 box, the query's own cell first.  A neighbouring cell is skipped
     // when a lower bound on the squared distance to anything assigned to it is already above
     // the best one: it can hold neither the minimum nor an equal distance with a lower index.

@@ -86,8 +86,8 @@ struct Job {
   float* loss_fwd;         // [Q] phi(d^2) of each forward query
   float* loss_rev;         // [2 max_pts] phi(d^2) of each reverse query (set 0 then set 1)
   float* loss_iso;         // [E] |r_e|
-  int* nn_fwd;             // [Q]
-  int* nn_rev;             // [2 max_pts]
+  int* nn_fwd;             // [Q] (-1 before the first search of a frame)
+  int* nn_rev;             // [2 max_pts] (-1 before the first search of a frame)
   float4* edge_d;          // [E] sgn(r) (y_i - y_j) / (|y_i - y_j| E)
   const int2* edges;       // [E]
   float* e_prev;           // [E] rest lengths from X_{t-1}

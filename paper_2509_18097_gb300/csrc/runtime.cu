@@ -668,6 +668,9 @@ pdg_status pdg_begin_frame(pdg_ctx* c, const float* target_xyz, int n_tgt, void*
   }
   CU(c, cudaMemsetAsync(J.step, 0, sizeof(int), s));
   CU(c, cudaMemsetAsync(J.status, 0, sizeof(int), s));
+  // no previous neighbours in a new frame (-1: the NN search starts cold)
+  CU(c, cudaMemsetAsync(J.nn_fwd, 0xff, sizeof(int) * (size_t)J.Q, s));
+  CU(c, cudaMemsetAsync(J.nn_rev, 0xff, sizeof(int) * 2 * (size_t)c->max_pts, s));
   CU(c, cudaMemsetAsync(J.loss, 0, 4 * sizeof(double), s));
   launch_tgt_build(c->dJ, J, s);
   launch_csr_build(c->dJ, J, s);
