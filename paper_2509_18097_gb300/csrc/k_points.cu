@@ -64,7 +64,7 @@ __global__ void k_plan(Plan* P) {
       if (J->lev[l].n > 128) t += J->lev[l].tiles;
       else {
         p3 += J->lev[l].n;
-        cols += 3 * ((J->lev[l].n * J->lev[l].n + 127) / 128);  // blocks of 128 columns
+        cols += 3 * ((J->lev[l].n * J->lev[l].n + 63) / 64);  // blocks of 64 columns (two threads each)
         ad += (J->lev[l].n3 + 3) >> 2;
       }
     }

@@ -348,62 +348,127 @@ __global__ void __launch_bounds__(PL_THREADS, 2) k_sobp(const Plan* __restrict__
 
 // ------------------------------------------------------------------------------ pass B
 
-// Pass B: the two tridiagonal solves T^2 h = g of one (kx, ky) column of one channel, with
-// the whole column in registers (N steps unrolled) and its reciprocal pivots in shared
-// memory.  T has diagonal b_i = a + lambda deg(i) (deg 1 at the two ends, 2 inside) and
-// off-diagonal -lambda, a = 1 + lambda (mu_kx + mu_ky).  Thomas: forward
-// r_i = 1 / (b_i + lambda c_{i-1}) with c_i = -lambda r_i, g'_i = (g_i + lambda g'_{i-1}) r_i;
-// backward h_{n-1} = g'_{n-1}, h_i = g'_i + lambda r_i h_{i+1}.  The column is read from
-// global memory once (z-planes without an active vertex as zero, without a load) and
-// written once (scaled by the 1/n^2 of the inverse x and y
-// transforms).  rs: this thread's pivots, stride COL_THREADS floats; volatile, so that the
-// compiler reloads them in every sweep instead of holding all N in registers beside the
-// column.  Consecutive threads take consecutive x, so every global access along z is
-// coalesced and every shared access conflict-free.
+// The two tridiagonal solves T^2 h = g of each (kx, ky) column of one channel.  T has
+// diagonal b_i = a + lambda deg(i) (deg 1 at the two ends, 2 inside), off-diagonal -lambda,
+// a = 1 + lambda (mu_kx + mu_ky).  Each solve is twisted (eliminated from both ends toward
+// the middle row m = n/2): the top thread of a column holds rows 0 .. m-1 and eliminates
+// downward, g'_i = (g_i + lambda g'_{i-1}) r_i; the bottom thread holds rows n-1 .. m and
+// eliminates upward with the mirrored pivots (T is persymmetric: the pivots from the bottom
+// are r_{n-1-i}); the middle row takes both neighbours,
+//   h_m = (g_m + lambda g'_{m-1} + lambda g''_{m+1}) / (b_m - lambda^2 (r_{m-1} + r_{m-2})),
+// and each thread back-substitutes toward its end, h_i = g'_i + lambda r_i h_{i +- 1}.  A
+// thread's chain is n/2 long, its half column lives in registers and its pivots are read
+// from the block's slice of a per-context table, staged in shared memory (volatile reads,
+// so the compiler keeps them out of registers).  The two threads of a column are lanes l and l + 16
+// of a warp (one value crosses between them, twice per solve); a warp covers 16 neighbouring
+// columns, so each row access is 64 contiguous bytes.  Rows of z-planes without an active
+// vertex are read as zero (the bit comes from a register mask, not from memory).
 constexpr int COL_THREADS = 128;
+constexpr int COLS_PER_ITEM = COL_THREADS / 2;
+constexpr int PIV_REGS = 16;  // pivots held in registers on the fast path (then the limit)
 
-template <int N>
-__device__ __forceinline__ void column_solve(float* __restrict__ t, const unsigned (&zb)[4], volatile float* rs,
-                                             float a, float lam, float scale) {
-  constexpr int n2 = N * N;
-  float v[N];
-#pragma unroll
-  for (int i = 0; i < N; ++i) v[i] = ((zb[i >> 5] >> (i & 31)) & 1u) ? t[i * n2] : 0.f;
-  float cp = 0.f, g = 0.f;
-#pragma unroll
-  for (int i = 0; i < N; ++i) {  // solve 1, forward (pivots)
-    const float b = a + lam * ((i == 0 || i == N - 1) ? 1.f : 2.f);
-    const float r = __frcp_rn(b + lam * cp);
-    rs[i * COL_THREADS] = r;
-    g = (v[i] + lam * g) * r;
-    v[i] = g;
-    cp = -lam * r;
-  }
-#pragma unroll
-  for (int i = N - 2; i >= 0; --i) v[i] = v[i] + lam * rs[i * COL_THREADS] * v[i + 1];  // solve 1, backward
-  g = 0.f;
-#pragma unroll
-  for (int i = 0; i < N; ++i) {  // solve 2, forward
-    g = (v[i] + lam * g) * rs[i * COL_THREADS];
-    v[i] = g;
-  }
-  t[(N - 1) * n2] = v[N - 1] * scale;
-#pragma unroll
-  for (int i = N - 2; i >= 0; --i) {  // solve 2, backward
-    v[i] = v[i] + lam * rs[i * COL_THREADS] * v[i + 1];
-    t[i * n2] = v[i] * scale;
+// Pivot table of a level: piv[j n^2 + col] = r_j for j < n/2 (downward Thomas pivots of T,
+// r_0 = 1 / b_0, r_j = 1 / (b_j - lambda^2 r_{j-1})) and, at j = n/2, the reciprocal of the
+// middle row's twisted pivot.  Computed in FP64 once per context (lambda and n are fixed).
+__global__ void k_sobz_pivots(float* __restrict__ piv, const float* __restrict__ mu, int n, float lam,
+                              int* __restrict__ slow) {
+  const int n2 = n * n, m = n / 2;
+  const double L = lam, L2 = (double)lam * lam;
+  for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < n2; col += gridDim.x * blockDim.x) {
+    const double a = 1.0 + L * ((double)mu[col % n] + (double)mu[col / n]);
+    double r = 0.0, rm1 = 0.0, rm2 = 0.0;
+    for (int j = 0; j < m; ++j) {
+      const double b = a + L * ((j == 0 || j == n - 1) ? 1.0 : 2.0);
+      r = 1.0 / (b - L2 * r);
+      piv[(size_t)j * n2 + col] = (float)r;
+      if (j == m - 1) rm1 = r;
+      if (j == m - 2) rm2 = r;
+    }
+    // row m: deg 1 only when it is the last row (n = 2); its lower neighbour exists for n >= 4
+    const double bm = a + L * ((m == n - 1) ? 1.0 : 2.0);
+    piv[(size_t)m * n2 + col] = (float)(1.0 / (bm - L2 * (rm1 + (n >= 4 ? rm2 : 0.0))));
+    // the pivots converge geometrically; the register path holds r_0 .. r_15 and the last one
+    // and needs every r_j, j >= 16, to equal the last one in FP32
+    bool same = true;
+    for (int j = PIV_REGS; j < m; ++j) same = same && piv[(size_t)j * n2 + col] == piv[(size_t)(m - 1) * n2 + col];
+    if (!same) atomicOr(slow, 1);
   }
 }
 
-// an item is COL_THREADS consecutive columns (col = y n + x) of one channel of one level
+void launch_sobz_pivots(float* piv, int* slow, const float* mu, int n, float lam, cudaStream_t s) {
+  if (n < 2 || n > 128) return;
+  const int n2 = n * n;
+  cudaMemsetAsync(slow, 0, sizeof(int), s);
+  k_sobz_pivots<<<(n2 + 127) / 128, 128, 0, s>>>(piv, mu, n, lam, slow);
+}
+
+// FAST: pivots r_0 .. r_{K-1} and the limit in registers, read once from the table `pg`;
+// otherwise each use reads the staged slice `pv` (stride COLS_PER_ITEM).
+template <int N, bool FAST>
+__device__ __forceinline__ void column_solve(float* __restrict__ t, const float* __restrict__ pg, volatile const float* pv,
+                                             const unsigned (&zb)[4], float lam, float scale, bool top, bool act) {
+  constexpr int M = N / 2;
+  constexpr int n2 = N * N;
+  constexpr int K = M < PIV_REGS ? M : PIV_REGS;
+  float rp[K], rinf = 0.f;
+  if (FAST) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) rp[k] = act ? __ldg(pg + k * n2) : 0.f;
+    rinf = act ? __ldg(pg + (M - 1) * n2) : 0.f;
+  }
+  auto piv = [&](int j) -> float { return FAST ? (j < K ? rp[j < K ? j : 0] : rinf) : pv[j * COLS_PER_ITEM]; };
+  const int J = top ? M : M - 1;  // rows this thread eliminates
+  float v[M];
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    const int i = top ? j : N - 1 - j;
+    v[j] = (act && ((zb[i >> 5] >> (i & 31)) & 1u)) ? t[i * n2] : 0.f;
+  }
+  const float rm = act ? (FAST ? __ldg(pg + M * n2) : pv[M * COLS_PER_ITEM]) : 0.f;
+#pragma unroll
+  for (int solve = 0; solve < 2; ++solve) {
+    float g = 0.f;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {  // elimination toward the middle
+      if (j < J) {
+        g = (v[j] + lam * g) * piv(j);
+        v[j] = g;
+      }
+    }
+    // middle row (held by the bottom thread): both eliminated neighbours
+    const float e_top = __shfl_xor_sync(0xffffffffu, v[M - 1], 16);  // top's g'_{m-1}
+    const float e_bot = M >= 2 ? v[M >= 2 ? M - 2 : 0] : 0.f;        // bottom's g''_{m+1}
+    float hm = (v[M - 1] + lam * e_top + lam * e_bot) * rm;  // meaningful in the bottom thread
+    const float hb = __shfl_xor_sync(0xffffffffu, hm, 16);
+    if (top) hm = hb;
+    else v[M - 1] = hm;
+    float h = hm;
+#pragma unroll
+    for (int j = M - 1; j >= 0; --j) {  // back substitution toward this thread's end
+      if (j < J) {
+        v[j] = v[j] + lam * piv(j) * h;
+        h = v[j];
+      }
+    }
+  }
+  if (act) {
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      const int i = top ? j : N - 1 - j;
+      t[i * n2] = v[j] * scale;
+    }
+  }
+}
+
+// an item is COLS_PER_ITEM consecutive columns (col = y n + x) of one channel of one level
 __device__ __forceinline__ bool column_item(const Job& J, int r, int& l, int& c, int& col0) {
   for (l = 0; l < J.L; ++l) {
     const int n = J.lev[l].n;
     if (n > 128) continue;
-    const int per = (n * n + COL_THREADS - 1) / COL_THREADS;
+    const int per = (n * n + COLS_PER_ITEM - 1) / COLS_PER_ITEM;
     if (r < 3 * per) {
       c = r / per;
-      col0 = (r - c * per) * COL_THREADS;
+      col0 = (r - c * per) * COLS_PER_ITEM;
       return true;
     }
     r -= 3 * per;
@@ -411,13 +476,14 @@ __device__ __forceinline__ bool column_item(const Job& J, int r, int& l, int& c,
   return false;
 }
 
-// One block of COL_THREADS per item.
-__global__ void __launch_bounds__(COL_THREADS, 3) k_sobz(const Plan* __restrict__ P) {
-  __shared__ float rs[128 * COL_THREADS];
-  __shared__ unsigned zbits[COL_THREADS / 32];
-  static_assert(COL_THREADS == 128, "one mask bit per z-plane of a 128^3 level");
+// One block of COL_THREADS per item: warp w covers columns col0 + 16 w .. + 15, lane l < 16
+// the top half of column l, lane l + 16 its bottom half.
+__global__ void __launch_bounds__(COL_THREADS, 4) k_sobz(const Plan* __restrict__ P) {
+  __shared__ unsigned zbits[4];
+  __shared__ float rs[(128 / 2 + 1) * COLS_PER_ITEM];  // pivots [j][column of the item]
   const int nj = P->n_jobs;
   const int total = P->pre[ST_COL][nj];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int it = blockIdx.x; it < total; it += gridDim.x) {
     const int j = find_job(P->pre[ST_COL], nj, it);
     const Job& J = *P->jobs[j];
@@ -427,33 +493,42 @@ __global__ void __launch_bounds__(COL_THREADS, 3) k_sobz(const Plan* __restrict_
     const Level& lv = J.lev[l];
     const int n = lv.n;
     if (n == 1) continue;  // a single vertex: T = 1
-    // bit i: z-plane i holds an active vertex (else it is zero and pass A did not write it);
-    // every load below is predicated on a register bit, none waits on the mask in memory
-    __syncthreads();  // the previous item has read zbits
+    const bool fast = !__ldg(lv.piv_slow);  // block-uniform
+    // bit i: z-plane i holds an active vertex (else it is zero and pass A did not write it)
+    __syncthreads();  // the previous item has read zbits and rs
     {
       const bool nz = threadIdx.x >= n || !lv.zmask || __ldg(lv.zmask + threadIdx.x);
       const unsigned b = __ballot_sync(0xffffffffu, nz);
-      if ((threadIdx.x & 31) == 0) zbits[threadIdx.x >> 5] = b;
+      if (lane == 0) zbits[warp] = b;
+      const int n2 = n * n, rows = fast ? 0 : n / 2 + 1;
+      for (int k = threadIdx.x; k < rows * COLS_PER_ITEM; k += COL_THREADS) {
+        const int cl = col0 + (k % COLS_PER_ITEM);
+        rs[k] = cl < n2 ? __ldg(lv.piv + (size_t)(k / COLS_PER_ITEM) * n2 + cl) : 0.f;
+      }
     }
     __syncthreads();
     const unsigned zb[4] = {zbits[0], zbits[1], zbits[2], zbits[3]};
-    const int col = col0 + threadIdx.x;
-    if (col >= n * n) continue;
-    const int x = col & (n - 1), y = col >> lv.lg;
+    const int col = col0 + warp * 16 + (lane & 15);
+    const bool act = col < n * n, top = lane < 16;
+    const int cc = act ? col : 0;
     const float lam = lv.lam;
-    const float a = 1.f + lam * (__ldg(lv.mu + x) + __ldg(lv.mu + y));
     const float scale = 1.f / (float)(n * n);
-    float* t = lv.tmp + (size_t)c * lv.n3 + col;
-    volatile float* r = rs + threadIdx.x;
-    switch (n) {
-      case 2: column_solve<2>(t, zb, r, a, lam, scale); break;
-      case 4: column_solve<4>(t, zb, r, a, lam, scale); break;
-      case 8: column_solve<8>(t, zb, r, a, lam, scale); break;
-      case 16: column_solve<16>(t, zb, r, a, lam, scale); break;
-      case 32: column_solve<32>(t, zb, r, a, lam, scale); break;
-      case 64: column_solve<64>(t, zb, r, a, lam, scale); break;
-      default: column_solve<128>(t, zb, r, a, lam, scale); break;
+    float* t = lv.tmp + (size_t)c * lv.n3 + cc;
+    const float* pg = lv.piv + cc;
+    volatile const float* pv = rs + warp * 16 + (lane & 15);
+#define PDG_SOLVE(NN)                                               \
+  if (fast) column_solve<NN, true>(t, pg, pv, zb, lam, scale, top, act); \
+  else column_solve<NN, false>(t, pg, pv, zb, lam, scale, top, act);
+    switch (n) {  // warp-uniform: every lane takes part in the exchanges
+      case 2: PDG_SOLVE(2) break;
+      case 4: PDG_SOLVE(4) break;
+      case 8: PDG_SOLVE(8) break;
+      case 16: PDG_SOLVE(16) break;
+      case 32: PDG_SOLVE(32) break;
+      case 64: PDG_SOLVE(64) break;
+      default: PDG_SOLVE(128) break;
     }
+#undef PDG_SOLVE
   }
 }
 

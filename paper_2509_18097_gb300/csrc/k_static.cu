@@ -17,16 +17,19 @@ namespace pdg {
 
 constexpr int STATIC_MAX_RES = PDG_STATIC_MAX_RES;
 constexpr size_t STATIC_N3 = (size_t)STATIC_MAX_RES * STATIC_MAX_RES * STATIC_MAX_RES;
-// layout: g (SoA, 3 n^3 floats) | tmp (3 n^3) | mu (n) | tw (n float2) | tw4 (n float2) |
-//         n_active (int) + bias (2 floats, read by the pass even when it skips Adam) | job | plan
+// layout: g (SoA, 3 n^3 floats) | tmp (3 n^3) | z-solve pivots ((n/2 + 1) n^2) | mu (n) | tw (n float2) | tw4 (n float2) |
+//         n_active (int) + bias (2 floats, read by the pass even when it skips Adam) | pivot flag | job | plan
 constexpr size_t SO_G = 0;
 constexpr size_t SO_TMP = SO_G + 3 * STATIC_N3 * sizeof(float);
-constexpr size_t SO_MU = SO_TMP + 3 * STATIC_N3 * sizeof(float);
+constexpr size_t SO_PIV = SO_TMP + 3 * STATIC_N3 * sizeof(float);
+constexpr size_t SO_MU =
+    SO_PIV + (size_t)(STATIC_MAX_RES / 2 + 1) * STATIC_MAX_RES * STATIC_MAX_RES * sizeof(float);
 constexpr size_t SO_TW = SO_MU + STATIC_MAX_RES * sizeof(float);
 constexpr size_t SO_TW4 = SO_TW + STATIC_MAX_RES * sizeof(float2);
 constexpr size_t SO_NA = SO_TW4 + STATIC_MAX_RES * sizeof(float2);
+constexpr size_t SO_SLOW = SO_NA + 4 * sizeof(int);  // after n_active and the two bias floats
 constexpr size_t SO_BIAS = SO_NA + sizeof(int);
-constexpr size_t SO_JOB = (SO_BIAS + 2 * sizeof(float) + 255) & ~size_t(255);
+constexpr size_t SO_JOB = (SO_SLOW + sizeof(int) + 255) & ~size_t(255);
 constexpr size_t SO_PLAN = (SO_JOB + sizeof(Job) + 255) & ~size_t(255);
 constexpr size_t SO_BYTES = (SO_PLAN + sizeof(Plan) + 255) & ~size_t(255);
 
@@ -103,6 +106,8 @@ extern "C" pdg_status pdg_precondition_static(int res, float lambda, const float
   lv.lam = lambda;
   lv.g = reinterpret_cast<float*>(base + SO_G);
   lv.tmp = reinterpret_cast<float*>(base + SO_TMP);
+  lv.piv = reinterpret_cast<float*>(base + SO_PIV);
+  lv.piv_slow = reinterpret_cast<int*>(base + SO_SLOW);
   lv.mu = reinterpret_cast<float*>(base + SO_MU);
   lv.tw = reinterpret_cast<float2*>(base + SO_TW);
   lv.tw4 = reinterpret_cast<float2*>(base + SO_TW4);
@@ -137,6 +142,7 @@ extern "C" pdg_status pdg_precondition_static(int res, float lambda, const float
       cudaMemcpyAsync(P.jobs[0], &J, sizeof(Job), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(base + SO_PLAN, &P, sizeof(Plan), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return PDG_ERR_CUDA;
+  launch_sobz_pivots(lv.piv, lv.piv_slow, lv.mu, n, lambda, s);
   const Plan* dP = reinterpret_cast<const Plan*>(base + SO_PLAN);
   launch_aos_to_soa(g, lv.g, n3, s);
   launch_plan(const_cast<Plan*>(dP), s);

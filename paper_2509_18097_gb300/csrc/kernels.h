@@ -45,6 +45,7 @@ int plane_smem_bytes(int n);
 int plane_smem_max(int nmax);
 void launch_aos_to_soa(const float* in, float* out, int n3, cudaStream_t s);
 void launch_zmask(Job* J, const Job& hJ, cudaStream_t s);
+void launch_sobz_pivots(float* piv, int* slow, const float* mu, int n, float lam, cudaStream_t s);
 
 // misc conversions
 void launch_soa_to_aos(const float* in, float* out, int n3, cudaStream_t s);

@@ -52,6 +52,8 @@ struct Level {
   float* g;       // [3][n3] dLoss/dTheta (zero at vertices no point touches)
   float* tmp;     // [3][n3] spectral work array (and preconditioned gradient in debug mode)
   int* zmask;     // [n] 1 for z-planes that hold an active vertex (per frame); null: all planes
+  float* piv;     // [(n/2 + 1) n^2] pivots of the z-direction twisted solves (n <= 128), per context
+  int* piv_slow;  // device flag: some pivot past the first 16 differs from the limit (no register path)
   float* mu;      // [n] eigenvalues 4 sin^2(pi k / 2n) of the 1-D path Laplacian
   float2* tw;     // [n] FFT twiddles exp(-2 pi i k / n)
   float2* tw4;    // [n] DCT twiddles exp(-i pi k / 2n)

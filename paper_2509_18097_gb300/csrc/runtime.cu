@@ -121,7 +121,7 @@ struct Layout {
   size_t total = 0;
   size_t job, plan, flag, stage, op_job, op_plan;
   struct Lv {
-    size_t theta, m, v, g, tmp, zmask, mu, tw, tw4, cnt, rowptr, flag, act_v, act_ptr, ent_p, ent_w, n_active, csum;
+    size_t theta, m, v, g, tmp, zmask, piv, piv_slow, mu, tw, tw4, cnt, rowptr, flag, act_v, act_ptr, ent_p, ent_w, n_active, csum;
     int cap;
   } lv[MAXL];
   size_t x, y, gfwd, gy, acc, loss_fwd, loss_rev, loss_iso, nn_fwd, nn_rev, edge_d, edges, e_prev, v2e_ptr, v2e;
@@ -152,6 +152,8 @@ Layout make_layout(const pdg_config& c, int V, int E, int max_pts) {
     v.g = a.take<float>(3 * n3);
     v.tmp = a.take<float>(3 * n3);
     v.zmask = a.take<int>(n);
+    v.piv = a.take<float>(n <= 128 ? (n / 2 + 1) * n * n : 1);
+    v.piv_slow = a.take<int>(1);
     v.mu = a.take<float>(n);
     v.tw = a.take<float2>(n);
     v.tw4 = a.take<float2>(n);
@@ -526,6 +528,8 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
     lv.g = (float*)P(o.g);
     lv.tmp = (float*)P(o.tmp);
     lv.zmask = (int*)P(o.zmask);
+    lv.piv = (float*)P(o.piv);
+    lv.piv_slow = (int*)P(o.piv_slow);
     lv.mu = (float*)P(o.mu);
     lv.tw = (float2*)P(o.tw);
     lv.tw4 = (float2*)P(o.tw4);
@@ -554,6 +558,7 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
         cudaMemcpyAsync(lv.tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(lv.tw4, tw4.data(), n * sizeof(float2), cudaMemcpyHostToDevice, s) != cudaSuccess)
       return bail(PDG_ERR_CUDA);
+    launch_sobz_pivots(lv.piv, lv.piv_slow, lv.mu, n, lv.lam, s);
   }
   J.x = (float4*)P(L.x);
   J.y = (float4*)P(L.y);
