@@ -185,9 +185,11 @@ Layout make_layout(const pdg_config& c, int V, int E, int max_pts) {
   L.src4 = a.take<float4>(max_pts);
   L.tgt4 = a.take<float4>(max_pts);
   L.verts4 = a.take<float4>(V);
-  L.tbits = grid_bits(max_pts);
-  // the moving grid is rebuilt every step (its offsets are a scan over all its cells):
-  // cells twice as wide as the target grid's, so the scan is 8 times shorter
+  // about 32 points per occupied cell in both NN grids: during a fit the nearest neighbour is
+  // often one or two spacings of a finer grid away, and the 3x3x3 box of these cells
+  // certifies almost every query in the one-thread-per-query pass (the moving grid is also
+  // rebuilt every step, its offsets a scan over all its cells)
+  L.tbits = grid_bits(max_pts, 32.0);
   L.mbits = grid_bits(std::max(V, max_pts), 32.0);
   const size_t tG3 = size_t(1) << (3 * L.tbits), mG3 = size_t(1) << (3 * L.mbits);
   L.t_hist = a.take<int>(tG3);
