@@ -206,9 +206,9 @@ pdg_status pdg_load_state(pdg_ctx* ctx, const void* host_buf, size_t n, void* cu
  * out = (I + lambda L)^{-2} g per channel on a res^3 vertex grid (L the free-boundary
  * 6-neighbour graph Laplacian), computed by the same preconditioner kernels as
  * pdg_precondition, without a context and without allocating: its scratch lives in one
- * fixed file-scope device array of about 9.5 MB (three res^3 x 3 float buffers at the maximum
- * res, plus small tables), which every GPU that loads the library keeps until the process
- * exits.
+ * fixed file-scope device array of about 6.5 MB (two res^3 x 3 float buffers and the z-solve
+ * pivot table at the maximum res, plus small tables), which every GPU that loads the library
+ * keeps until the process exits.
  *  - g, out: DEVICE pointers to float [res^3][3] ((z*res + y)*res + x); host pointers give
  *    PDG_ERR_INVALID.  res: 1 or a power of two up to PDG_STATIC_MAX_RES; larger grids give
  *    PDG_ERR_BUDGET (use pdg_precondition).  lambda: finite, >= 0.

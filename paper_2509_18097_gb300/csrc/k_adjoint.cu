@@ -143,23 +143,39 @@ __device__ __forceinline__ void row_sum(const Level& lv, const float4* __restric
   const int* __restrict__ ep = lv.ent_p;
   const float* __restrict__ ew = lv.ent_w;
   constexpr int B = 8;
-  for (int k = s; k < e; k += B * step) {
-    int p[B];
-    float wt[B];
+  if (s >= e) return;
+  int p[B];
+  float wt[B];
 #pragma unroll
-    for (int u = 0; u < B; ++u) {
-      const int kk = min(k + u * step, e - 1);  // past the end: reload the last entry, weight 0
-      p[u] = __ldg(ep + kk);
-      wt[u] = k + u * step < e ? __ldg(ew + kk) * sc : 0.f;  // exact: sc is a power of two
-    }
+  for (int u = 0; u < B; ++u) {
+    const int kk = min(s + u * step, e - 1);  // past the end: reload the last entry, weight 0
+    p[u] = __ldg(ep + kk);
+    wt[u] = s + u * step < e ? __ldg(ew + kk) * sc : 0.f;  // exact: sc is a power of two
+  }
+  for (int k = s; k < e; k += B * step) {
     float4 g[B];
 #pragma unroll
     for (int u = 0; u < B; ++u) g[u] = __ldg(gy + p[u]);
+    // the next batch's entries are loaded while this batch's gathers are in flight
+    const int kn = k + B * step;
+    int pn[B];
+    float wn[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int kk = min(kn + u * step, e - 1);
+      pn[u] = __ldg(ep + kk);
+      wn[u] = kn + u * step < e ? __ldg(ew + kk) * sc : 0.f;
+    }
 #pragma unroll
     for (int u = 0; u < B; ++u) {
       ax += round_to_ll(__fmul_rn(wt[u], g[u].x));
       ay += round_to_ll(__fmul_rn(wt[u], g[u].y));
       az += round_to_ll(__fmul_rn(wt[u], g[u].z));
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      p[u] = pn[u];
+      wt[u] = wn[u];
     }
   }
 }
