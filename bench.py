@@ -414,7 +414,7 @@ def main():
     dom = max(prof, key=prof.get)
     bound, amount, unit = stage_model(dom, Q, V, M, E, w.res, act)
     if bound == "alu":
-        amount = candidate_flops(y, V, w.target.astype(np.float64), grid_bits(M), grid_bits(max(V, M), 32.0))
+        amount = candidate_flops(y, V, w.target.astype(np.float64), grid_bits(M, 32.0), grid_bits(max(V, M), 32.0))
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
         achieved = amount / (prof[dom] / 1e3) / 1e12
