@@ -61,8 +61,7 @@ __global__ void k_csr_fill(Job* __restrict__ Jp) {
       const int K = corners(J, lv, x.x, x.y, x.z, vid, w);
       for (int c = 0; c < K; ++c) {
         const int pos = lv.rowptr[vid[c]] + atomicSub(&lv.cnt[vid[c]], 1) - 1;
-        lv.ent_p[pos] = p;
-        lv.ent_w[pos] = w[c] * invL;
+        lv.ent[pos] = make_int2(p, __float_as_int(w[c] * invL));
       }
     }
   }
@@ -140,8 +139,7 @@ __device__ __forceinline__ long long round_to_ll(float x) {
 
 __device__ __forceinline__ void row_sum(const Level& lv, const float4* __restrict__ gy, int s, int e, int step,
                                         float sc, long long& ax, long long& ay, long long& az) {
-  const int* __restrict__ ep = lv.ent_p;
-  const float* __restrict__ ew = lv.ent_w;
+  const int2* __restrict__ en = lv.ent;
   constexpr int B = 8;
   if (s >= e) return;
   int p[B];
@@ -149,8 +147,9 @@ __device__ __forceinline__ void row_sum(const Level& lv, const float4* __restric
 #pragma unroll
   for (int u = 0; u < B; ++u) {
     const int kk = min(s + u * step, e - 1);  // past the end: reload the last entry, weight 0
-    p[u] = __ldg(ep + kk);
-    wt[u] = s + u * step < e ? __ldg(ew + kk) * sc : 0.f;  // exact: sc is a power of two
+    const int2 t = __ldg(en + kk);
+    p[u] = t.x;
+    wt[u] = s + u * step < e ? __int_as_float(t.y) * sc : 0.f;  // exact: sc is a power of two
   }
   for (int k = s; k < e; k += B * step) {
     float4 g[B];
@@ -163,8 +162,9 @@ __device__ __forceinline__ void row_sum(const Level& lv, const float4* __restric
 #pragma unroll
     for (int u = 0; u < B; ++u) {
       const int kk = min(kn + u * step, e - 1);
-      pn[u] = __ldg(ep + kk);
-      wn[u] = kn + u * step < e ? __ldg(ew + kk) * sc : 0.f;
+      const int2 t = __ldg(en + kk);
+      pn[u] = t.x;
+      wn[u] = kn + u * step < e ? __int_as_float(t.y) * sc : 0.f;
     }
 #pragma unroll
     for (int u = 0; u < B; ++u) {

@@ -63,8 +63,7 @@ struct Level {
   int* flag;      // [n3 + 1] active-vertex flags, then their exclusive prefix
   int* act_v;     // [cap] active vertices (ascending)
   int* act_ptr;   // [cap + 1] entry range of each active vertex
-  int* ent_p;     // [8 Q] point of each entry
-  float* ent_w;   // [8 Q] trilinear weight / L
+  int2* ent;      // [8 Q] entries: (point, bits of the trilinear weight / L)
   int* n_active;  // device scalar
   int* csum;      // scan scratch
   int adj_lg;     // adjoint: log2 of the lanes per row, 6 = a block per row (set by the plan kernel)

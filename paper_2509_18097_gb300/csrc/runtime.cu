@@ -121,7 +121,7 @@ struct Layout {
   size_t total = 0;
   size_t job, plan, flag, stage, op_job, op_plan;
   struct Lv {
-    size_t theta, m, v, g, tmp, zmask, piv, piv_slow, mu, tw, tw4, cnt, rowptr, flag, act_v, act_ptr, ent_p, ent_w, n_active, csum;
+    size_t theta, m, v, g, tmp, zmask, piv, piv_slow, mu, tw, tw4, cnt, rowptr, flag, act_v, act_ptr, ent, n_active, csum;
     int cap;
   } lv[MAXL];
   size_t x, y, gfwd, gy, acc, loss_fwd, loss_rev, loss_iso, nn_fwd, nn_rev, edge_d, edges, e_prev, v2e_ptr, v2e;
@@ -162,8 +162,7 @@ Layout make_layout(const pdg_config& c, int V, int E, int max_pts) {
     v.flag = a.take<int>(n3 + 1);
     v.act_v = a.take<int>(v.cap);
     v.act_ptr = a.take<int>(v.cap + 1);
-    v.ent_p = a.take<int>(8 * (size_t)Q);
-    v.ent_w = a.take<float>(8 * (size_t)Q);
+    v.ent = a.take<int2>(8 * (size_t)Q);
     v.n_active = a.take<int>(1);
     v.csum = a.take<int>((n3 + 1) / SCAN_CHUNK + 2);
   }
@@ -540,8 +539,7 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
     lv.flag = (int*)P(o.flag);
     lv.act_v = (int*)P(o.act_v);
     lv.act_ptr = (int*)P(o.act_ptr);
-    lv.ent_p = (int*)P(o.ent_p);
-    lv.ent_w = (float*)P(o.ent_w);
+    lv.ent = (int2*)P(o.ent);
     lv.n_active = (int*)P(o.n_active);
     lv.csum = (int*)P(o.csum);
     c->nmax = std::max(c->nmax, n);
