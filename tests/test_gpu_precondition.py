@@ -51,6 +51,31 @@ def test_cosine_modes_scale_by_closed_form(n):
     H.check_close(f"modes n={n}", out, exp)
 
 
+@pytest.mark.parametrize("n", [64, 128])
+def test_cosine_modes_with_slowly_converging_pivots(n):
+    """lambda = 8: the z-solve pivots reach their FP32 limit only after about 28 rows, so
+    the solves read every pivot from the table instead of holding 16 plus the limit in
+    registers; the result must be the same closed form."""
+    from paper_2509_18097_gb300 import binding as B
+
+    lam = 8.0
+    ks = [(0, 0, 0), (1, 2, 0), (0, 0, 1), (n // 2, 1, n - 1), (3, n - 1, 5)]
+    g = np.zeros((n**3, 3), np.float64)
+    exp = np.zeros_like(g)
+    for c in range(3):
+        for j, k in enumerate(ks):
+            a = (1.0 + j + c) * (-1) ** j
+            m = mode(n, k)
+            g[:, c] += a * m
+            exp[:, c] += a * factor(n, k, lam) * m
+    ctx = ctx_for(B, n, lam0=lam)
+    try:
+        out = B.pdg_precondition(ctx, 0, g.astype(np.float32), np.empty((n**3, 3), np.float32))
+    finally:
+        B.pdg_destroy(ctx)
+    H.check_close(f"modes lambda=8 n={n}", out, exp)
+
+
 @pytest.mark.parametrize("n", [4, 16, 32])
 def test_random_gradient_matches_oracle_cg(n):
     from paper_2509_18097_gb300 import binding as B
