@@ -292,9 +292,12 @@ def run_reference(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": world,
             "steps": n, "warmup": 0, "ms_per_step": 1000 * dt / n, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "config": {"workload": WORKLOAD, "parallelism": "single", "l2": "n/a (CPU)", "grids": list(w.res),
+                       "steps_per_frame": STEPS_PER_FRAME, "V": len(w.template), "N": len(w.source),
+                       "M": len(w.target), "E": len(w.edges)},
             "cpu_baseline": {"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{n} full oracle steps of the headline workload (numpy FP64, single thread)"},
+                             "sample": f"{n} full oracle steps of the headline workload (numpy FP64, single "
+                                       f"thread; at most 2 steps of about 15 s each, no warm-up)"},
             "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
