@@ -271,11 +271,11 @@ void launch_stage(int i, const Plan* plan, int nmax, int sms, cudaStream_t s, in
     case 0: launch_interp(plan, grid, s, bump); break;
     case 1: launch_mov_scan(plan, sms * 2, s); break;
     case 2: launch_mov_scatter(plan, grid, s); break;
-    case 3: launch_nn(plan, grid, s); break;
+    case 3: launch_nn(plan, grid * 2, s); break;
     case 4: launch_nn_hard(plan, sms * 4, s); break;
     case 5: launch_iso_edges(plan, grid, s); break;
     case 6: launch_assemble(plan, grid, s); break;
-    case 7: launch_adjoint(plan, grid, s); break;
+    case 7: launch_adjoint(plan, grid * 2, s); break;
     case 8:
     case 9:
     case 10:
