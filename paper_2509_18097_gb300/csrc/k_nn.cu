@@ -3,13 +3,15 @@
 // sets) against the target cloud, and the target cloud against each moving set.
 //
 // The target (per frame) and the moving sets (per step) are counting-sorted into uniform
-// cell grids (see CellGrid).  A first kernel searches every query's 3x3x3 cell box with
-// one thread per query, queries taken in cell order so neighbouring lanes read the same
-// cells (cells that cannot beat the best distance found so far are skipped).  The answer is
-// certified when the best squared distance is below the squared
-// distance from the query to the box's open faces (with a margin covering the rounding of
-// the cell assignment); otherwise the query is appended to a per-job list that a second,
-// warp-cooperative kernel searches ring by ring (lanes split the rows of each shell, a
+// cell grids (see CellGrid, about 32 points per occupied cell).  A first kernel searches
+// every query's 3x3x3 cell box with one thread per query, starting from the query's
+// neighbour of the previous step, queries taken in cell order so neighbouring lanes read the
+// same cells (cells that cannot beat the best distance found so far are skipped).  The
+// answer is certified when the best squared distance is below the squared distance from the
+// query to the searched box's open faces (with a margin covering the rounding of the cell
+// assignment); otherwise the same thread searches the next shell (up to NN_RTHREAD), and a
+// query still uncertified is appended to a per-job list that a second, warp-cooperative
+// kernel searches ring by ring (lanes split the rows of each shell, a
 // __shfl min-reduction over (d^2, index) packed in 64 bits picks the lexicographic minimum,
 // i.e. the lowest index on ties), falling back to an exhaustive scan of the set beyond
 // NN_RMAX rings.  Both kernels compare candidates with the same fp32 expression, so the
