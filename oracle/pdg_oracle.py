@@ -8,10 +8,14 @@ plain, slow re-statement of what the paper defines, written in numpy float64, wi
 library primitives (scipy's k-d tree as a candidate generator, numpy reductions) used
 only as steps whose result is then checked exactly.
 
-Every function cites the passage it follows.  Readings of passages that are silent or
-garbled (displacement payload, vertex-aligned levels, Neumann 6-neighbour Laplacian,
-preconditioning before Adam, lowest-index tie break, ...) are the ones listed in the
-design notes; each is repeated at the function that depends on it.
+Every function cites the passage it follows.  Where the paper is silent or garbled the
+oracle takes one reading, stated at the function that depends on it: a 3-float
+displacement payload per grid vertex (Sec. 3.1/3.3), levels whose vertices are aligned with
+the domain corners and points clamped to the domain (Eq. 1), the free-boundary unit-weight
+6-neighbour graph Laplacian (Sec. 3.2), the raw gradient preconditioned and then fed to
+Adam (Sec. 3.2 Eq. 3 with Sec. 3.6), a differentiated robust weight (Sec. 3.4), the
+lowest index winning a nearest-neighbour tie, sgn(0) = 0 at the isometry kink, and every
+frame starting from zero grids and fresh Adam state.
 
 Layout conventions (shared only as *conventions* with the CUDA path):
   * a level with n vertices per axis is an array [n, n, n, 3] indexed [z, y, x, channel],
@@ -61,6 +65,11 @@ class Config:
     eps: float = EPS
     precondition: bool = True
     robust_weight_stopgrad: bool = False
+    payload: str = "displacement"  # or "cayley": the 6-D rotation + translation of Sec. 3.3
+
+    @property
+    def channels(self) -> int:
+        return 6 if self.payload == "cayley" else 3
 
     def lr(self, l: int) -> float:
         """Learning rate of level l (0 = coarsest), Sec. 3.6; x0.1 without preconditioning."""
@@ -114,16 +123,18 @@ def _corners(x, lo, hi, n):
 def eval_displacement(x, thetas, lo, hi):
     """u(x) = (1/L) sum_l sum_{c in N^l(x)} w^{l,c}(x) T^{l,c}   (Sec. 3.1, Eq. 1).
 
-    Reading: the per-vertex payload is a 3-vector displacement (the hot path's payload),
-    levels are averaged (not residual), values live on grid vertices.
-    thetas: list of [n, n, n, 3] arrays.  Returns [N, 3] float64.
+    Reading: levels are averaged (not residual), values live on grid vertices.  The payload
+    has C channels: a 3-vector displacement (the default payload) or the 6-D Cayley
+    rotation + translation of Sec. 3.3.
+    thetas: list of [n, n, n, C] arrays.  Returns [N, C] float64.
     """
     x = np.asarray(x, F64)
     L = len(thetas)
-    u = np.zeros((len(x), 3), F64)
+    C = np.asarray(thetas[0]).shape[-1]
+    u = np.zeros((len(x), C), F64)
     for th in thetas:
         n = th.shape[0]
-        flat = np.asarray(th, F64).reshape(-1, 3)
+        flat = np.asarray(th, F64).reshape(-1, C)
         idx, w = _corners(x, lo, hi, n)
         u += (w[:, :, None] * flat[idx]).sum(1)
     return u / L
@@ -143,14 +154,76 @@ def interp_adjoint(x, g_pts, res, lo, hi):
     """
     g_pts = np.asarray(g_pts, F64)
     L = len(res)
+    C = g_pts.shape[1]
     out = []
     for n in res:
         idx, w = _corners(x, lo, hi, n)
-        G = np.zeros((n * n * n, 3), F64)
+        G = np.zeros((n * n * n, C), F64)
         for c in range(idx.shape[1]):
             np.add.at(G, idx[:, c], w[:, c : c + 1] * g_pts / L)
-        out.append(G.reshape(n, n, n, 3))
+        out.append(G.reshape(n, n, n, C))
     return out
+
+
+# ---------------------------------------------------------------------------------------
+# the 6-D payload of Sec. 3.3: Cayley rotation + translation per grid vertex
+# ---------------------------------------------------------------------------------------
+
+
+def skew(z):
+    """The skew-symmetric matrix Z of z (Sec. 3.3): rows (0, -z2, z1), (z2, 0, -z0),
+    (-z1, z0, 0).  z: [..., 3] -> [..., 3, 3]."""
+    z = np.asarray(z, F64)
+    Z = np.zeros(z.shape[:-1] + (3, 3), F64)
+    Z[..., 0, 1], Z[..., 0, 2] = -z[..., 2], z[..., 1]
+    Z[..., 1, 0], Z[..., 1, 2] = z[..., 2], -z[..., 0]
+    Z[..., 2, 0], Z[..., 2, 1] = -z[..., 1], z[..., 0]
+    return Z
+
+
+def cayley(z):
+    """R(z) = (I + Z)(I - Z)^{-1}, the Cayley parameterisation of a rotation (Sec. 3.3).
+    z: [..., 3] -> [..., 3, 3]."""
+    Z = skew(z)
+    I = np.broadcast_to(np.eye(3), Z.shape)
+    return (I + Z) @ np.linalg.inv(I - Z)
+
+
+def apply_transform(x, T):
+    """M(T) x for the 4x4 homogeneous matrix [[R(z), t], [0, 1]] of T = [z, t] (Sec. 3.3),
+    without the homogeneous coordinate: R(z) x + t.  Reading: the rotation acts about the
+    world origin, as the matrix product is written.  x: [N, 3], T: [N, 6] -> [N, 3]."""
+    x = np.asarray(x, F64)
+    T = np.asarray(T, F64)
+    return np.einsum("nij,nj->ni", cayley(T[:, :3]), x) + T[:, 3:]
+
+
+def apply_transform_backward(x, T, g):
+    """dLoss/dT given dLoss/dy = g for y = R(z) x + t: dLoss/dt = g and, by the product rule
+    on R = (I + Z)(I - Z)^{-1} with dZ/dz_k = E_k (the skew matrix of the k-th unit vector),
+    dR/dz_k = E_k (I - Z)^{-1} + (I + Z)(I - Z)^{-1} E_k (I - Z)^{-1}, so
+    dLoss/dz_k = g . (dR/dz_k x).  Returns [N, 6]."""
+    x = np.asarray(x, F64)
+    T = np.asarray(T, F64)
+    g = np.asarray(g, F64)
+    Z = skew(T[:, :3])
+    I = np.broadcast_to(np.eye(3), Z.shape)
+    Ainv = np.linalg.inv(I - Z)
+    R = (I + Z) @ Ainv
+    out = np.zeros((len(x), 6), F64)
+    for k in range(3):
+        Ek = skew(np.eye(3)[k])
+        dR = Ek @ Ainv + R @ Ek @ Ainv
+        out[:, k] = np.einsum("ni,nij,nj->n", g, dR, x)
+    out[:, 3:] = g
+    return out
+
+
+def deform_cayley(x, thetas, lo, hi):
+    """x_t = M(T_t(x_{t-1})) x_{t-1}: one factor of the recursive product of Sec. 3.3, with
+    T_t = (1/L) sum_l trilerp(G^l, x) the averaged 6-D payload (Eq. 1).  thetas: list of
+    [n, n, n, 6] arrays (z first, then t)."""
+    return apply_transform(x, eval_displacement(x, thetas, lo, hi))
 
 
 # ---------------------------------------------------------------------------------------
@@ -358,6 +431,30 @@ def sobolev_precondition(g, lam, tol=1e-14):
     return _cg_shifted(h, lam, tol)
 
 
+def sobolev_precondition_spectral(g, lam):
+    """(I + lam L)^{-2} g per channel by the eigen-decomposition of L (Sec. 3.2, Eq. 3).
+
+    Reading of the Laplacian as the free-boundary 6-neighbour graph Laplacian of the vertex
+    grid: it is the Kronecker sum of three path-graph Laplacians, whose orthonormal
+    eigenvectors are the DCT-II basis vectors with eigenvalues 4 sin^2(pi k / 2n).  So
+    (I + lam L)^{-2} = C^T diag((1 + lam (mu_kx + mu_ky + mu_kz))^{-2}) C with C the
+    orthonormal 3-D DCT-II, which scipy's dctn applies as a library step.  Same operator
+    as sobolev_precondition (CG); used where a level is too large for CG to finish in
+    seconds.  g: [nz, ny, nx, C]."""
+    from scipy.fft import dctn, idctn
+
+    g = np.asarray(g, F64)
+    if lam == 0:
+        return g.copy()
+    mus = [4.0 * np.sin(np.pi * np.arange(n) / (2.0 * n)) ** 2 for n in g.shape[:3]]
+    mu = mus[0][:, None, None] + mus[1][None, :, None] + mus[2][None, None, :]
+    f = (1.0 + lam * mu) ** -2
+    out = np.empty_like(g)
+    for c in range(g.shape[3]):
+        out[..., c] = idctn(f * dctn(g[..., c], type=2, norm="ortho"), type=2, norm="ortho")
+    return out
+
+
 def adam_update(theta, m, v, g, k, lr, beta1=BETA1, beta2=BETA2, eps=EPS):
     """One Adam step (Sec. 3.6: default hyper-parameters), PyTorch semantics:
     m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
@@ -400,7 +497,7 @@ def begin_frame(template_prev, source_prev, target, edges, cfg: Config, thetas=N
     P = np.asarray(source_prev, F64)
     x = np.concatenate([X, P], 0)
     if thetas is None:
-        thetas = [np.zeros((n, n, n, 3), F64) for n in cfg.res]
+        thetas = [np.zeros((n, n, n, cfg.channels), F64) for n in cfg.res]
     else:
         thetas = [np.asarray(t, F64).copy() for t in thetas]
     return FrameState(
@@ -417,7 +514,7 @@ def begin_frame(template_prev, source_prev, target, edges, cfg: Config, thetas=N
 
 def step(st: FrameState, cfg: Config, update: bool = True) -> dict:
     """One optimisation iteration (the hot path):
-    (a) y = x + u(x) on Q (Eq. 1, Sec. 3.3);
+    (a) y = x + u(x) on Q (Eq. 1, Sec. 3.3), or y = R(z(x)) x + t(x) with the Cayley payload;
     (b) CD_R(X_hat, P_t) and CD_R(P_hat, P_t) with gradients (Sec. 3.4, L_transform with
         T = 1 and the confidence weight as the scalar w_chamfer_mesh);
     (c) w_iso * L_iso (Sec. 3.4);
@@ -425,18 +522,24 @@ def step(st: FrameState, cfg: Config, update: bool = True) -> dict:
     (e) (I + lambda_l L_l)^{-2} per level (Eq. 3), then Adam with lr_l (Sec. 3.6).
     Returns a dict of every intermediate (for parity tests)."""
     V = st.n_verts
-    y = deform(st.x, st.thetas, cfg.lo, cfg.hi)
+    if cfg.payload == "cayley":
+        T = eval_displacement(st.x, st.thetas, cfg.lo, cfg.hi)
+        y = apply_transform(st.x, T)
+    else:
+        y = deform(st.x, st.thetas, cfg.lo, cfg.hi)
     YX, PH = y[:V], y[V:]
     cm = robust_chamfer(YX, st.target, cfg.alpha, cfg.robust_weight_stopgrad)
     cp = robust_chamfer(PH, st.target, cfg.alpha, cfg.robust_weight_stopgrad)
     iso, giso = isometry(YX, st.edges, st.e_prev)
     loss = cfg.w_chamfer_mesh * cm["loss"] + cfg.w_chamfer_pts * cp["loss"] + cfg.w_iso * iso
     g_pts = np.concatenate([cfg.w_chamfer_mesh * cm["grad_A"] + cfg.w_iso * giso, cfg.w_chamfer_pts * cp["grad_A"]], 0)
-    grads = interp_adjoint(st.x, g_pts, cfg.res, cfg.lo, cfg.hi)
+    # with the Cayley payload the point gradients go through y = R(z) x + t first
+    g_T = apply_transform_backward(st.x, T, g_pts) if cfg.payload == "cayley" else g_pts
+    grads = interp_adjoint(st.x, g_T, cfg.res, cfg.lo, cfg.hi)
     pgrads = []
     for l, g in enumerate(grads):
         pgrads.append(sobolev_precondition(g, cfg.lam(l)) if cfg.precondition else g.copy())
-    out = dict(y=y, loss=loss, cd_mesh=cm["loss"], cd_pts=cp["loss"], iso=iso, g_pts=g_pts, grads=grads,
+    out = dict(y=y, loss=loss, cd_mesh=cm["loss"], cd_pts=cp["loss"], iso=iso, g_pts=g_pts, g_T=g_T, grads=grads,
                pgrads=pgrads, chamfer_mesh=cm, chamfer_pts=cp)
     if update:
         st.k += 1
@@ -447,9 +550,11 @@ def step(st: FrameState, cfg: Config, update: bool = True) -> dict:
 
 
 def end_frame(st: FrameState, cfg: Config):
-    """Frame end (Sec. 3.3): X_t = X_{t-1} + u_t(X_{t-1}) with the final grids; the
-    target becomes the next frame's source.  Returns (X_t, P_t)."""
-    X = deform(st.x[: st.n_verts], st.thetas, cfg.lo, cfg.hi)
+    """Frame end (Sec. 3.3): X_t = M(T_t(X_{t-1})) X_{t-1} with the final grids (for the
+    displacement payload X_{t-1} + u_t(X_{t-1})); the target becomes the next frame's
+    source.  Returns (X_t, P_t)."""
+    xv = st.x[: st.n_verts]
+    X = deform_cayley(xv, st.thetas, cfg.lo, cfg.hi) if cfg.payload == "cayley" else deform(xv, st.thetas, cfg.lo, cfg.hi)
     return X, st.target.copy()
 
 

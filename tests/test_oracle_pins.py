@@ -149,6 +149,62 @@ def test_nn_exact_matches_bruteforce(kind):
     np.testing.assert_array_equal(d1, d2)
 
 
+def second_gap_bruteforce(q, b):
+    """Relative gap (d2_second - d2_best) / d2_second from the full distance matrix: the
+    best is the lexicographic (d2, index) minimum, the second the smallest d2 of every
+    other point (equal to the best for exact ties and duplicates)."""
+    D = ((q[:, None, :] - b[None, :, :]) ** 2).sum(-1)
+    best = D.argmin(1)
+    d1 = D[np.arange(len(q)), best]
+    D[np.arange(len(q)), best] = np.inf
+    d2 = D.min(1)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return np.where(d2 > 0, (d2 - d1) / np.where(d2 > 0, d2, 1.0), 0.0)
+
+
+@pytest.mark.parametrize("kind", ["random", "lattice", "duplicates", "pairs"])
+def test_nn_second_gap_matches_bruteforce(kind):
+    """The near-tie measure that decides which GPU index mismatches are excused: the
+    relative gap between the best and the second-best squared distance, against the
+    full distance matrix.  Lattices and duplicates give exact ties (gap 0); 'pairs' places
+    each query almost midway between two points (gaps of 1e-9 .. 1e-3)."""
+    r = rng(31)
+    if kind == "random":
+        b = r.uniform(-1, 1, (800, 3))
+        q = r.uniform(-1.2, 1.2, (600, 3))
+    elif kind == "lattice":
+        b = r.integers(-3, 4, (500, 3)).astype(float)
+        q = r.integers(-6, 7, (600, 3)) / 2.0
+    elif kind == "duplicates":
+        base = r.uniform(-1, 1, (200, 3))
+        b = np.concatenate([base, base[:70], r.uniform(-1, 1, (100, 3))])
+        q = np.concatenate([base[:150] + 1e-3 * r.standard_normal((150, 3)), r.uniform(-1, 1, (200, 3))])
+    else:
+        q = r.uniform(-1, 1, (300, 3))
+        u1 = r.standard_normal((300, 3))
+        u2 = r.standard_normal((300, 3))
+        u1 /= np.linalg.norm(u1, axis=1, keepdims=True)
+        u2 /= np.linalg.norm(u2, axis=1, keepdims=True)
+        eps = 10.0 ** r.uniform(-9, -3, 300)
+        d = 1e-3
+        b = np.concatenate([q + d * u1, q + d * (1 + eps[:, None]) * u2, r.uniform(-1, 1, (200, 3))])
+    idx, d2 = O.nn_exact(q, b)
+    gap = O.nn_second_gap(q, b, idx, d2)
+    ref = second_gap_bruteforce(q, b)
+    np.testing.assert_allclose(gap, ref, rtol=1e-9, atol=1e-15)
+    if kind in ("lattice", "duplicates"):
+        assert (ref == 0).sum() > 20  # exact ties are present and reported as gap 0
+    if kind == "pairs":
+        assert ((ref > 0) & (ref < 1e-6)).sum() > 20  # near-ties below the GPU tests' threshold
+
+
+def test_nn_second_gap_single_point_set():
+    q = rng(32).uniform(-1, 1, (5, 3))
+    b = np.array([[0.1, 0.2, 0.3]])
+    idx, d2 = O.nn_exact(q, b)
+    assert np.all(np.isinf(O.nn_second_gap(q, b, idx, d2)))
+
+
 # --------------------------------------------------------------------------------- Chamfer
 
 
@@ -294,6 +350,31 @@ def test_sobolev_scales_cosine_mode_by_closed_form(n, k, lam):
     np.testing.assert_allclose(out, f * g, atol=1e-12)
 
 
+@pytest.mark.parametrize("n,k,lam", [(8, (1, 0, 0), 0.25), (12, (3, 5, 2), 0.84375), (16, (15, 1, 9), 2.0)])
+def test_sobolev_spectral_scales_cosine_mode_by_closed_form(n, k, lam):
+    c = cosine_mode(n, k)
+    g = np.stack([c, 2 * c, -c], -1)
+    f = (1 + lam * mode_eigenvalue(n, k)) ** -2
+    np.testing.assert_allclose(O.sobolev_precondition_spectral(g, lam), f * g, atol=1e-12)
+
+
+def test_sobolev_spectral_equals_cg_solve():
+    """The eigen-decomposition form and the two CG solves apply the same operator; on a
+    non-cubic-looking random field with zero regions (as a grid gradient) they agree to
+    rounding."""
+    r = rng(15)
+    n = 10
+    g = r.standard_normal((n, n, n, 3))
+    g[r.random((n, n, n)) < 0.5] = 0.0
+    for lam in (0.0, 0.375, 1.6875):
+        a = O.sobolev_precondition(g, lam)
+        b = O.sobolev_precondition_spectral(g, lam)
+        np.testing.assert_allclose(b, a, atol=1e-11 * np.abs(g).max())
+        # and it solves (I + lam L)^2 b = g
+        A = lambda v: v + lam * O.grid_laplacian(v)
+        np.testing.assert_allclose(A(A(b)), g, atol=1e-10 * np.abs(g).max())
+
+
 def test_sobolev_identity_sum_symmetry():
     r = rng(14)
     n = 9
@@ -423,3 +504,126 @@ def test_synthetic_workload_sizes():
     assert (len(v), len(f), len(e)) == (20000, 40000, 60000)
     v, f, e = synth.geodesic_sphere(12)
     assert (len(v), len(f), len(e)) == (10 * 144 + 2, 20 * 144, 30 * 144)
+
+
+# --------------------------------------------------------------------------------- Cayley payload
+
+
+def test_cayley_zero_is_identity():
+    np.testing.assert_array_equal(O.cayley(np.zeros((4, 3))), np.broadcast_to(np.eye(3), (4, 3, 3)))
+    x = rng(40).uniform(-1.4, 1.4, (300, 3))
+    th = [np.zeros((n, n, n, 6)) for n in (3, 6)]
+    np.testing.assert_array_equal(O.deform_cayley(x, th, LO, HI), x)
+
+
+def test_cayley_is_a_rotation():
+    """R(z) is orthogonal with determinant 1 for any z."""
+    z = rng(41).standard_normal((500, 3)) * 2.0
+    R = O.cayley(z)
+    np.testing.assert_allclose(R @ np.swapaxes(R, 1, 2), np.broadcast_to(np.eye(3), R.shape), atol=1e-13)
+    np.testing.assert_allclose(np.linalg.det(R), 1.0, atol=1e-13)
+
+
+def test_cayley_matches_axis_angle_rotation():
+    """z = tan(theta / 2) a (unit axis a) is the rotation by theta about a, against scipy's
+    rotation-vector routine and, for a = e_z, the matrix written out by hand."""
+    from scipy.spatial.transform import Rotation
+
+    th = 0.7
+    R = O.cayley(np.array([[0.0, 0.0, math.tan(th / 2)]]))[0]
+    c, s_ = math.cos(th), math.sin(th)
+    np.testing.assert_allclose(R, [[c, -s_, 0], [s_, c, 0], [0, 0, 1]], atol=1e-15)
+    r = rng(42)
+    a = r.standard_normal((50, 3))
+    a /= np.linalg.norm(a, axis=1, keepdims=True)
+    ang = r.uniform(-3.0, 3.0, 50)
+    R = O.cayley(np.tan(ang / 2)[:, None] * a)
+    np.testing.assert_allclose(R, Rotation.from_rotvec(ang[:, None] * a).as_matrix(), atol=1e-12)
+
+
+def test_cayley_translation_only_equals_displacement_payload():
+    """With z = 0 on every level the 6-D payload is a pure translation: the same points as
+    the displacement payload holding t."""
+    r = rng(43)
+    x = r.uniform(-1.4, 1.4, (400, 3))
+    t = [r.standard_normal((n, n, n, 3)) * 0.05 for n in (4, 7)]
+    th6 = [np.concatenate([np.zeros_like(a), a], -1) for a in t]
+    np.testing.assert_allclose(O.deform_cayley(x, th6, LO, HI), O.deform(x, t, LO, HI), atol=1e-15)
+
+
+def test_cayley_backward_matches_finite_differences():
+    r = rng(44)
+    x = r.uniform(-1, 1, (60, 3))
+    T = r.standard_normal((60, 6)) * 0.4
+    g = r.standard_normal((60, 3))
+    an = O.apply_transform_backward(x, T, g)
+    h = 1e-6
+    for k in range(6):
+        Tp, Tm = T.copy(), T.copy()
+        Tp[:, k] += h
+        Tm[:, k] -= h
+        fd = ((O.apply_transform(x, Tp) - O.apply_transform(x, Tm)) * g).sum(1) / (2 * h)
+        np.testing.assert_allclose(an[:, k], fd, rtol=1e-7, atol=1e-8)
+
+
+def test_cayley_recursion_is_the_product_of_homogeneous_matrices():
+    """Two frames of the recursion of Sec. 3.3 (each frame's payload evaluated at the
+    previous frame's points) equal M(T_2(x_1)) M(T_1(x_0)) x_0 with the 4x4 matrices
+    multiplied out."""
+    r = rng(45)
+    x0 = r.uniform(-1, 1, (80, 3))
+    g1 = [r.standard_normal((n, n, n, 6)) * 0.1 for n in (3, 5)]
+    g2 = [r.standard_normal((n, n, n, 6)) * 0.1 for n in (4,)]
+    x1 = O.deform_cayley(x0, g1, LO, HI)
+    x2 = O.deform_cayley(x1, g2, LO, HI)
+
+    def M(T):
+        out = np.zeros((len(T), 4, 4))
+        out[:, :3, :3] = O.cayley(T[:, :3])
+        out[:, :3, 3] = T[:, 3:]
+        out[:, 3, 3] = 1.0
+        return out
+
+    M1 = M(O.eval_displacement(x0, g1, LO, HI))
+    M2 = M(O.eval_displacement(x1, g2, LO, HI))
+    h = np.concatenate([x0, np.ones((80, 1))], 1)
+    np.testing.assert_allclose(np.einsum("nij,njk,nk->ni", M2, M1, h)[:, :3], x2, atol=1e-14)
+
+
+def test_cayley_step_gradient_matches_finite_differences():
+    """The whole step with the 6-D payload: the grid gradient (through y = R(z) x + t, the
+    adjoint of Eq. 1 on 6 channels) equals central differences of the total loss."""
+    v, e, src, tgt = small_problem()
+    cfg = O.Config(res=(3, 5), payload="cayley")
+    r = rng(46)
+    thetas = [r.standard_normal((n, n, n, 6)) * 0.02 for n in cfg.res]
+    st = O.begin_frame(v, src, tgt, e, cfg, thetas)
+    base = O.step(st, cfg, update=False)
+
+    def loss_at(ths):
+        s2 = O.begin_frame(v, src, tgt, e, cfg, ths)
+        o = O.step(s2, cfg, update=False)
+        sgn = np.sign(O.edge_lengths(o["y"][: len(v)], e) - st.e_prev)
+        return o, sgn
+
+    _, sgn0 = loss_at(thetas)
+    h = 1e-6
+    checked = 0
+    for l, n in enumerate(cfg.res):
+        g = base["grads"][l].reshape(-1)
+        for flat in np.argsort(-np.abs(g))[:12]:
+            tp = [t.copy() for t in thetas]
+            tm = [t.copy() for t in thetas]
+            tp[l].reshape(-1)[flat] += h
+            tm[l].reshape(-1)[flat] -= h
+            (op, sp), (om, sm) = loss_at(tp), loss_at(tm)
+            same = all(np.array_equal(o[c][k], base[c][k]) for o in (op, om)
+                       for c in ("chamfer_mesh", "chamfer_pts") for k in ("nn_ab", "nn_ba"))
+            if not (same and np.array_equal(sp, sgn0) and np.array_equal(sm, sgn0)):
+                continue
+            fd = (op["loss"] - om["loss"]) / (2 * h)
+            assert abs(fd - g[flat]) <= 1e-6 * max(abs(fd), 1e-3), (l, flat, fd, g[flat])
+            checked += 1
+    assert checked >= 12
+    # both halves of the payload receive gradient
+    assert np.abs(base["grads"][1][..., :3]).max() > 0 and np.abs(base["grads"][1][..., 3:]).max() > 0
