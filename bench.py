@@ -107,41 +107,10 @@ class ClockSampler:
 # ------------------------------------------------------------------------------ helpers
 
 
-def candidate_flops(y, V, target, tbits, mbits, lo=-1.5, hi=1.5):
-    """Distance evaluations of the one-ring search (8 flops each): for every query the
-    number of points in its 3x3x3 cell box, computed from the same cell grids (the target
-    grid for the forward queries, the moving grid for the reverse ones)."""
-    import numpy as np
-
-    def cells(p, G):
-        c = np.floor((p - lo) * (G / (hi - lo))).astype(np.int64)
-        return np.clip(c, 0, G - 1)
-
-    def box_counts(pts, G):
-        c = cells(pts, G)
-        h = np.zeros((G + 2, G + 2, G + 2), np.int64)
-        np.add.at(h, (c[:, 2] + 1, c[:, 1] + 1, c[:, 0] + 1), 1)
-        b = np.zeros_like(h)
-        for dz in (-1, 0, 1):
-            for dy in (-1, 0, 1):
-                for dx in (-1, 0, 1):
-                    b += np.roll(np.roll(np.roll(h, dz, 0), dy, 1), dx, 2)
-        return b
-
-    def lookup(b, q, G):
-        c = cells(q, G)
-        return b[c[:, 2] + 1, c[:, 1] + 1, c[:, 0] + 1].sum()
-
-    Gt, Gm = 1 << tbits, 1 << mbits
-    n = lookup(box_counts(target, Gt), y, Gt)  # forward: template + source into the target
-    n += lookup(box_counts(y[:V], Gm), target, Gm) + lookup(box_counts(y[V:], Gm), target, Gm)
-    return 8.0 * float(n)
-
-
 # kernel of each profiled stage and the source file that defines it
 STAGE_KERNEL = {
     "interp": ("k_interp", "k_points.cu"), "mov_scatter": ("k_mov_scatter", "k_points.cu"),
-    "nn": ("k_nn", "k_nn.cu"), "nn_hard": ("k_nn_hard", "k_nn.cu"), "adjoint": ("k_adjoint", "k_adjoint.cu"),
+    "nn_fwd": ("k_nn", "k_nn.cu"), "nn_rev": ("k_nn", "k_nn.cu"), "nn_hard": ("k_nn_hard", "k_nn.cu"), "adjoint": ("k_adjoint", "k_adjoint.cu"),
     "sob_xy_fwd": ("k_sobp", "k_sobolev_plane.cu"), "sob_z": ("k_sobz", "k_sobolev_plane.cu"),
     "sob_xy_inv": ("k_sobp_inv", "k_sobolev_plane.cu"), "adam": ("k_adam", "k_sobolev_plane.cu"),
     "iso_edges": ("k_iso_edges", "k_points.cu"),
@@ -207,22 +176,22 @@ def active_vertices(x, res, lo=-1.5, hi=1.5):
 
 def stage_model(stage, Q, V, M, E, res, act):
     """Algorithmic work of one launch of a stage: (bound, amount, unit).  Bytes count the
-    data the operation must move once (12 B per point or grid value, 4 B per scalar)."""
-    G = sum(n**3 for n in res if n <= 128)
+    data the operation must move once (12 B per point or grid value, 4 B per scalar).  The
+    three Sobolev passes have no bytes of their own: the preconditioner's algorithmic
+    minimum is one read and one write of the gradient per level, counted once in the
+    preconditioner + Adam row (see step_model); their passes over the spectrum are
+    implementation cost."""
+    G = sum(n**3 for n in res)
     A = sum(act)
-    if stage == "sob_xy_fwd":  # read g, write the x/y spectrum
-        return "hbm", G * 24, "B"
-    if stage == "sob_z":  # read and write the spectrum once
-        return "hbm", G * 24, "B"
-    if stage == "sob_xy_inv":  # read the solved spectrum, write the preconditioned gradient
-        return "hbm", G * 24, "B"
+    if stage in ("sob_xy_fwd", "sob_z", "sob_xy_inv", "sobolev_256"):
+        return "hbm", None, "B"
     if stage == "adam":  # read the preconditioned gradient, read+write theta, m, v
         return "hbm", G * (12 + 3 * 24), "B"
     if stage == "interp":  # read x, write y, read each touched grid value
         return "hbm", Q * 24 + A * 12, "B"
-    if stage == "adjoint":  # read x and dL/dy, write each touched grid gradient
-        return "hbm", Q * 24 + A * 12, "B"
-    if stage in ("nn", "nn_hard"):
+    if stage == "adjoint":  # read dL/dy (16 B per point), write each touched grid gradient
+        return "hbm", Q * 16 + A * 12, "B"
+    if stage in ("nn_fwd", "nn_rev", "nn_hard"):
         return "alu", None, "FLOP"
     if stage == "iso_edges":
         return "hbm", E * (8 + 4 + 4 + 12) + V * 12, "B"
@@ -238,23 +207,30 @@ def stage_model(stage, Q, V, M, E, res, act):
     return "hbm", 0, "B"
 
 
+def step_model(Q, V, M, E, res, act):
+    """Algorithmic bytes of one whole step by the hot-path rows (12 B per point or grid value):
+    (a) read x, write y, each touched grid value once; (b) per query 16 B in and 8 B out, and
+    the per-step re-sort of the moving points (read, key, write); (c) edge indices and rest
+    lengths, vertex positions; (d) read the point gradients, write each touched grid
+    gradient; (e) the preconditioner + Adam fused minimum, 8 G (read g, read and write theta,
+    m and v, G = 12 B per grid vertex summed over the levels).  Returns (total, parts)."""
+    G = sum(n**3 for n in res) * 12
+    A = sum(act) * 12
+    parts = {"a_eval": 24 * Q + A, "b_chamfer": 24 * (Q + 2 * M) + 3 * 16 * Q, "c_isometry": 12 * E + 16 * V,
+             "d_adjoint": 16 * Q + A, "e_precondition_adam": 8 * G}
+    return sum(parts.values()), parts
+
+
 # ------------------------------------------------------------------------------ serving
 
 
-def run_serving(n_seq=16, n_frames=3, steps=100, rate_hz=400.0, scale=0.2, budget_gb=150.0):
+def run_serving(n_seq=32, n_frames=2, steps=100, rate_hz=100.0, scale=1.0, budget_gb=150.0):
     """Served frames/s and p50/p99 per-frame latency: continuous batching vs the plain
     one-frame-at-a-time form, on the same Poisson trace (sequences drawn like the batched
     workload, points per frame scaled by `scale`)."""
-    import numpy as np
+    from paper_2509_18097_gb300 import serve
 
-    from paper_2509_18097_gb300 import serve, synth
-
-    seqs = []
-    for i in range(n_seq):
-        jb = synth.batched_job(i, scale=scale)
-        frames = [jb["frame"](k, n_frames + 1) for k in range(n_frames + 1)]
-        mp = max(len(f) for f in frames)
-        seqs.append(serve.Sequence(i, jb["template"], jb["edges"], frames[0], frames[1:], jb["res"], mp))
+    seqs = serving_sequences(n_seq, n_frames, scale=scale)
     out = {"sequences": n_seq, "frames": n_seq * n_frames, "steps_per_frame": steps, "rate_hz": rate_hz,
            "points_per_frame": [int(min(len(f) for s_ in seqs for f in s_.frames)),
                                 int(max(len(f) for s_ in seqs for f in s_.frames))],
@@ -269,35 +245,123 @@ def run_serving(n_seq=16, n_frames=3, steps=100, rate_hz=400.0, scale=0.2, budge
     return out
 
 
+def serving_sequences(n_seq, n_frames, scale=1.0, big_every=0, big_pts=500_000):
+    """Sequences drawn like the batched workload (synth.batched_job); every `big_every`-th one
+    (if > 0) has `big_pts`-point frames."""
+    from paper_2509_18097_gb300 import serve, synth
+
+    seqs = []
+    for i in range(n_seq):
+        big = big_every > 0 and i % big_every == big_every - 1
+        jb = synth.batched_job(i, scale=scale, n_pts=big_pts if big else None)
+        frames = [jb["frame"](k, n_frames + 1) for k in range(n_frames + 1)]
+        mp = max(len(f) for f in frames)
+        seqs.append(serve.Sequence(i, jb["template"], jb["edges"], frames[0], frames[1:], jb["res"], mp))
+    return seqs
+
+
+def run_serving_scale(steps=100, budget_gb=150.0):
+    """The batched workload (64 sequences, 10 frames, every frame requested at once) and the
+    served trace (256 sequences, 5% with 500k-point frames, Poisson arrivals at 50-400 req/s),
+    each in the continuous-batching server and one frame at a time.  Minutes of GPU time."""
+    from paper_2509_18097_gb300 import serve
+
+    out = {}
+    seqs = serving_sequences(64, 10)
+    trace_b = [serve.Request(s.sid, k, 0.0) for s in seqs for k in range(len(s.frames))]
+    trace_p = [serve.Request(s.sid, k, 0.0) for s in seqs for k in range(len(s.frames))]
+    srv = serve.Server(seqs, steps=steps, budget_bytes=int(budget_gb * 1e9), max_slots=64)
+    b = srv.run(trace_b, realtime=False)
+    srv.close()
+    p = serve.serve_plain(seqs, trace_p, steps, realtime=False)
+    out["batched_64x10"] = {"sequences": 64, "frames": len(trace_b), "steps_per_frame": steps,
+                            "batched": {k: b[k] for k in ("frames_per_s", "wall_s")},
+                            "plain": {k: p[k] for k in ("frames_per_s", "wall_s")}}
+    seqs = serving_sequences(256, 2, big_every=20)
+    out["served_256"] = {"sequences": 256, "frames_per_sequence": 2, "big_500k_sequences": 256 // 20,
+                         "budget_gb": budget_gb, "rates": {}}
+    for rate in (50.0, 100.0, 200.0, 400.0):
+        r = {}
+        for mode in ("batched", "plain"):
+            tr = serve.poisson_trace(seqs, rate, seed=7)
+            if mode == "batched":
+                srv = serve.Server(seqs, steps=steps, budget_bytes=int(budget_gb * 1e9), max_slots=256)
+                st = srv.run(tr, realtime=True)
+                srv.close()
+            else:
+                st = serve.serve_plain(seqs, tr, steps, realtime=True)
+            r[mode] = {"frames_per_s": st["frames_per_s"], "p50_ms": 1e3 * st["p50_s"], "p99_ms": 1e3 * st["p99_s"],
+                       "wall_s": st["wall_s"]}
+        out["served_256"]["rates"][str(int(rate))] = r
+        print(json.dumps({"rate": rate, **r}), flush=True)
+    return out
+
+
 # ------------------------------------------------------------------------------ reference arm
 
 
-def run_reference(args, world, rank):
-    import numpy as np
-
+def _oracle_steps(n):
+    """n FP64 oracle steps of the headline workload in this process (single-threaded numpy);
+    returns the seconds they took (set-up excluded)."""
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
     from oracle import pdg_oracle as O
+    from paper_2509_18097_gb300 import synth
+
+    w = synth.ellipsoid_pair(seed=0, theta_sigma=0)
+    cfg = O.Config(res=w.res)
+    st = O.begin_frame(w.template, w.source, w.target, w.edges, cfg)
+    t0 = time.perf_counter()
+    for _ in range(n):
+        O.step(st, cfg)
+    return time.perf_counter() - t0
+
+
+def oracle_baseline(n_single=1):
+    """The oracle on the host's cores: one process (one core) for `n_single` steps, then one
+    step in each of nproc spawned single-threaded processes at once (nproc independent
+    frame fits, the throughput the host's cores give); memory permitting, else fewer."""
+    import multiprocessing as mp
+
+    t1 = _oracle_steps(n_single)
+    cores = os.cpu_count() or 1
+    try:
+        import psutil
+
+        cores = max(1, min(cores, int(psutil.virtual_memory().available / 4e9)))  # ~3 GB per oracle step
+    except Exception:
+        pass
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_steps, [1] * cores)
+    tn = time.perf_counter() - t0
+    return {"single": {"value": n_single / t1, "cores": 1, "seconds": t1},
+            "all_cores": {"value": cores / tn, "cores": cores, "seconds": tn}}
+
+
+def run_reference(args, world, rank):
     from paper_2509_18097_gb300 import synth
 
     if rank != 0:
         return
     w = synth.ellipsoid_pair(seed=0, theta_sigma=0)
-    cfg = O.Config(res=w.res)
     n = max(1, min(args.steps, 2))
-    st = O.begin_frame(w.template, w.source, w.target, w.edges, cfg)
-    t0 = time.perf_counter()
-    for _ in range(n):
-        O.step(st, cfg)
-    dt = time.perf_counter() - t0
-    v = n / dt
+    base = oracle_baseline(n)
+    v = base["all_cores"]["value"]
+    dt = base["all_cores"]["seconds"] / base["all_cores"]["cores"]
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": world,
-            "steps": n, "warmup": 0, "ms_per_step": 1000 * dt / n, "higher_is_better": True, "scaling": "weak",
+            "steps": n, "warmup": 0, "ms_per_step": 1000.0 / v, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "parallelism": "single", "l2": "n/a (CPU)", "grids": list(w.res),
                        "steps_per_frame": STEPS_PER_FRAME, "V": len(w.template), "N": len(w.source),
                        "M": len(w.target), "E": len(w.edges)},
-            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{n} full oracle steps of the headline workload (numpy FP64, single "
-                                       f"thread; at most 2 steps of about 15 s each, no warm-up)"},
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": base["all_cores"]["cores"], "kind": "oracle",
+                             "sample": f"one full FP64 oracle step of the headline workload in each of "
+                                       f"{base['all_cores']['cores']} spawned single-threaded processes at once "
+                                       f"(independent fits); one process alone: {base['single']['value']:.4f} "
+                                       f"steps/s over {n} steps",
+                             "single_core": base["single"]},
             "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -314,6 +378,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=10)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-scale", action="store_true",
+                    help="only the batched (64 x 10 frames) and served (256 sequences, 4 rates) runs; minutes")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -328,6 +394,11 @@ def main():
     import torch
 
     import __graft_entry__
+
+    if args.serving_scale:
+        __graft_entry__.build()
+        print(json.dumps({"serving_scale": run_serving_scale()}), flush=True)
+        return
 
     dist = None
     if world > 1:
@@ -410,25 +481,22 @@ def main():
     prof = B.pdg_profile_step(ctx, args.profile_steps)
     prof = {k: v / args.profile_steps for k, v in prof.items()}
     y = B.pdg_read(ctx, B.BUF_Y, 0, np.empty((Q, 3), np.float32)).astype(np.float64)
+    # squared distances the NN search evaluated, counted by the kernels themselves over the
+    # next steps of the same frame (counting is off while the stages are timed)
+    B.pdg_set_debug(ctx, False, count_nn=True)
+    cands = []
+    for _ in range(args.profile_steps):
+        B.pdg_step(ctx, 1)
+        cands.append(int(B.pdg_read(ctx, B.BUF_COUNTERS, 0, np.empty(4, np.uint64))[0]))
+    B.pdg_set_debug(ctx, False, count_nn=False)
     B.pdg_end_frame(ctx)
+    nn_cands = float(np.mean(cands))
     act = active_vertices(np.concatenate([w.template, w.source]).astype(np.float64), w.res)
     hbm_peak, sm_max, peak_kind = load_peaks()
     sm_mhz = clocks["sm_mhz"] or sm_max
-    dom = max(prof, key=prof.get)
-    bound, amount, unit = stage_model(dom, Q, V, M, E, w.res, act)
-    if bound == "alu":
-        amount = candidate_flops(y, V, w.target.astype(np.float64), grid_bits(M, 32.0), grid_bits(max(V, M), 32.0))
-        sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
-        achieved = amount / (prof[dom] / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": measured_traffic(dom), "kernel": STAGE_KERNEL.get(dom, (dom,))[0],
-                "peak_note": f"FP32 {sms} SMs x 128 FMA x 2 at {sm_mhz:.0f} MHz (measured clock)"}
-    else:
-        achieved = amount / (prof[dom] / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": measured_traffic(dom), "kernel": STAGE_KERNEL.get(dom, (dom,))[0],
-                "algorithmic_bytes": amount, "peak_note": f"{peak_kind} copy bandwidth (burst)"}
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+    nn_ms = prof["nn_fwd"] + prof["nn_rev"] + prof["nn_hard"]
     stages = {}
     for k, ms in prof.items():
         b_, a_, u_ = stage_model(k, Q, V, M, E, w.res, act)
@@ -437,6 +505,38 @@ def main():
             st["GB/s"] = round(a_ / (ms / 1e3) / 1e9, 1)
             st["frac_hbm"] = round(a_ / (ms / 1e3) / 1e9 / hbm_peak, 3)
         stages[k] = st
+    sob_ms = sum(prof[k] for k in ("sob_xy_fwd", "sob_z", "sob_xy_inv", "adam", "sobolev_256"))
+    G_bytes = sum(n**3 for n in w.res) * 12
+    stages["precondition_adam"] = {"ms": round(sob_ms, 4), "GB/s": round(8 * G_bytes / (sob_ms / 1e3) / 1e9, 1),
+                                   "frac_hbm": round(8 * G_bytes / (sob_ms / 1e3) / 1e9 / hbm_peak, 3),
+                                   "algorithmic_bytes": 8 * G_bytes, "note": "8 G of the fused (e) row; the four kernels' time"}
+    stages["nn_search"] = {"ms": round(nn_ms, 4), "candidates_per_step": nn_cands,
+                           "TFLOP/s": round(8 * nn_cands / (nn_ms / 1e3) / 1e12, 3),
+                           "frac_fp32": round(8 * nn_cands / (nn_ms / 1e3) / 1e12 / fp32_peak, 4)}
+    grouped = dict(prof)
+    grouped["nn"] = nn_ms  # the search's three passes form one stage of the step
+    for k in ("nn_fwd", "nn_rev", "nn_hard"):
+        grouped.pop(k)
+    dom = max(grouped, key=grouped.get)
+    bound, amount, unit = stage_model("nn_fwd" if dom == "nn" else dom, Q, V, M, E, w.res, act)
+    if bound == "alu":
+        amount = 8.0 * nn_cands
+        achieved = amount / (nn_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                "traffic": measured_traffic("nn_fwd"), "kernel": "k_nn (forward + reverse) + k_nn_hard",
+                "algorithmic_flops": amount,
+                "peak_note": f"FP32 {sms} SMs x 128 FMA x 2 at {sm_mhz:.0f} MHz (measured clock); 8 FLOP per squared "
+                             f"distance the search evaluated ({nn_cands:.4g} per step, counted by the kernels)"}
+    else:
+        achieved = amount / (prof[dom] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": measured_traffic(dom), "kernel": STAGE_KERNEL.get(dom, (dom,))[0],
+                "algorithmic_bytes": amount, "peak_note": f"{peak_kind} copy bandwidth (burst)"}
+    step_bytes, step_parts = step_model(Q, V, M, E, w.res, act)
+    whole_step = {"algorithmic_bytes": step_bytes, "parts": step_parts, "ms_per_step": ms_per_step,
+                  "GB/s": step_bytes / (ms_per_step / 1e3) / 1e9,
+                  "frac_hbm": step_bytes / (ms_per_step / 1e3) / 1e9 / hbm_peak,
+                  "ceiling_steps_per_s": hbm_peak * 1e9 / step_bytes}
 
     # end to end through the C-ABI with host buffers: pinned target in, vertices + stats out
     tgt_host = torch.from_numpy(w.target.copy()).pin_memory()
@@ -466,15 +566,13 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        from oracle import pdg_oracle as O
-
-        cfgo = O.Config(res=w.res)
-        st = O.begin_frame(w.template, w.source, w.target, w.edges, cfgo)
-        t0 = time.perf_counter()
-        O.step(st, cfgo)
-        dt = time.perf_counter() - t0
-        cpu = {"value": 1.0 / dt, "unit": "steps/s", "cores": 1, "kind": "oracle",
-               "sample": "1 full FP64 oracle step of the headline workload (numpy, single thread)"}
+        base = oracle_baseline(1)  # spawned processes: nothing forked after the GPU work
+        cpu = {"value": base["all_cores"]["value"], "unit": "steps/s", "cores": base["all_cores"]["cores"],
+               "kind": "oracle",
+               "sample": f"one full FP64 oracle step of the headline workload in each of "
+                         f"{base['all_cores']['cores']} spawned single-threaded processes at once (independent "
+                         f"fits); one process alone: {base['single']['value']:.4f} steps/s",
+               "single_core": base["single"]}
 
     if rank == 0:
         line = {
@@ -486,7 +584,7 @@ def main():
                        "steps_per_frame": STEPS_PER_FRAME,
                        "V": V, "N": N, "M": M, "E": E},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
-            "roofline": roof, "cpu_baseline": cpu, "stages": stages,
+            "roofline": roof, "cpu_baseline": cpu, "stages": stages, "whole_step": whole_step,
             "resident_l2_steps_per_s": 1000.0 / resident_ms, "wall_s_timed": wall, "serving": serving,
         }
         print(json.dumps(line), flush=True)

@@ -27,7 +27,8 @@
  *    cloud, target); caller buffers need only live for the call.  Output buffers are
  *    caller-allocated.
  *  - Grid level l (0 = coarsest) has res[l] vertices per axis spanning [lo, hi] with
- *    corners aligned; its values are float32 [res^3][3] indexed ((z*res + y)*res + x).
+ *    corners aligned; its values are float32 [res^3][C] indexed ((z*res + y)*res + x), C = 3
+ *    (displacement payload) or 6 (Cayley payload, see pdg_config.payload).
  */
 #ifndef PDG_H
 #define PDG_H
@@ -70,7 +71,17 @@ typedef struct pdg_config {
   int precondition;           /* 1: (I + lambda L)^{-2} (Eq. 3); 0: raw gradient, lr x 0.1 */
   int robust_weight_stopgrad; /* 1: the robust weight is not differentiated */
   int warm_start;             /* 1: a frame starts from the previous frame's grids */
+  int payload;                /* PDG_PAYLOAD_DISPLACEMENT (0) or PDG_PAYLOAD_CAYLEY (1), see below */
 } pdg_config;
+
+/* Payload of a grid vertex.  DISPLACEMENT: 3 floats u, a point moves to x + u(x) (the
+ * rotation part of Sec. 3.3 held at the identity).  CAYLEY: the 6-D vector T = (z, t) of
+ * Sec. 3.3; the averaged T(x) (Eq. 1) moves x to R(z) x + t with R(z) = (I + Z)(I - Z)^{-1},
+ * Z the skew-symmetric matrix of z (rotation about the world origin).  Level values are then
+ * float [res^3][6] ordered (z0, z1, z2, t0, t1, t2), and every level must have at most 128
+ * vertices per axis (PDG_ERR_INVALID otherwise). */
+#define PDG_PAYLOAD_DISPLACEMENT 0
+#define PDG_PAYLOAD_CAYLEY 1
 
 /* Losses of the last iteration of a frame (evaluated before that iteration's update). */
 typedef struct pdg_fit_stats {
@@ -80,6 +91,9 @@ typedef struct pdg_fit_stats {
   double iso;        /* L_iso (unweighted) */
   int n_steps;       /* iterations run in the frame */
   int status;        /* pdg_status of the frame */
+  int nn_ties;       /* nearest-neighbour queries of the last iteration whose neighbour was decided
+                        by an exact tie of fp32 squared distances (the lowest index won; a reading,
+                        the paper does not say how ties break) */
 } pdg_fit_stats;
 
 typedef struct pdg_ctx pdg_ctx;
@@ -129,20 +143,24 @@ pdg_status pdg_get_vertices(pdg_ctx* ctx, float* out_xyz, void* cuda_stream);
 /* Inspection of internal buffers (tests, autograd, debugging); out may be host or device.
  * `level` is used by the per-level buffers.  out_bytes must be at least the size given. */
 enum pdg_buffer {
-  PDG_BUF_THETA = 0,    /* level values, float [res^3][3] */
-  PDG_BUF_GRAD = 1,     /* dLoss/dTheta of the last step, float [res^3][3] */
-  PDG_BUF_PGRAD = 2,    /* preconditioned gradient of the last step, float [res^3][3]
+  PDG_BUF_THETA = 0,    /* level values, float [res^3][C] (C = 3, or 6 with the Cayley payload) */
+  PDG_BUF_GRAD = 1,     /* dLoss/dTheta of the last step, float [res^3][C] */
+  PDG_BUF_PGRAD = 2,    /* preconditioned gradient of the last step, float [res^3][C]
                            (only kept when pdg_set_debug(ctx, 1) was called) */
   PDG_BUF_Y = 3,        /* deformed query points y of the last step, float [n_verts+n_src][3] */
   PDG_BUF_POINT_GRAD = 4, /* dLoss/dy of the last step, float [n_verts+n_src][3] */
   PDG_BUF_NN_FWD = 5,   /* int32 [n_verts+n_src]: nearest target point of each query */
   PDG_BUF_NN_REV = 6,   /* int32 [2][n_tgt]: nearest template vertex / source point of each target point */
   PDG_BUF_LOSS = 7,     /* double [4]: total, cd_mesh, cd_pts, iso of the last step */
-  PDG_BUF_SOURCE = 8    /* current source cloud P_{t-1}, float [n_src][3] */
+  PDG_BUF_SOURCE = 8,   /* current source cloud P_{t-1}, float [n_src][3] */
+  PDG_BUF_COUNTERS = 9  /* uint64 [4] of the last step: squared distances the nearest-neighbour
+                           search evaluated (counted only with PDG_DEBUG_COUNT_NN, else 0),
+                           queries decided by an exact tie, queries left to the warp-cooperative
+                           ring search, 0 */
 };
 pdg_status pdg_read(pdg_ctx* ctx, int which, int level, void* out, size_t out_bytes, void* cuda_stream);
 
-/* Overwrites level `level`'s values with theta (float [res^3][3], host or device) and
+/* Overwrites level `level`'s values with theta (float [res^3][C], host or device) and
  * resets its Adam moments.  Valid inside a frame (used to start from given grids). */
 pdg_status pdg_write_theta(pdg_ctx* ctx, int level, const float* theta, void* cuda_stream);
 
@@ -175,8 +193,20 @@ pdg_status pdg_eval(pdg_ctx* ctx, double* loss, void* cuda_stream);
  * gradient buffers are used as scratch): PDG_ERR_STATE inside a frame.  Synchronises. */
 pdg_status pdg_precondition(pdg_ctx* ctx, int level, const float* g, float* out, void* cuda_stream);
 
-/* 1: keep the preconditioned gradient of each step readable as PDG_BUF_PGRAD. */
-pdg_status pdg_set_debug(pdg_ctx* ctx, int keep_pgrad);
+/* Debug flags (bitwise or), applied to the following steps without re-capturing the step:
+ * PDG_DEBUG_KEEP_PGRAD keeps the preconditioned gradient of each step readable as
+ * PDG_BUF_PGRAD; PDG_DEBUG_COUNT_NN counts the squared distances the nearest-neighbour search
+ * evaluates (PDG_BUF_COUNTERS[0]; one warp-aggregated atomic per query warp, so leave it off
+ * while timing).  Unknown bits: PDG_ERR_INVALID.  Synchronises the device. */
+#define PDG_DEBUG_KEEP_PGRAD 1
+#define PDG_DEBUG_COUNT_NN 2
+pdg_status pdg_set_debug(pdg_ctx* ctx, int flags);
+
+/* Test hook: the library's next n device allocations (context arenas, batch tables) fail as
+ * if the device were out of memory, so that callers can exercise their PDG_ERR_OOM paths;
+ * the failing call frees whatever it had already taken.  n <= 0 turns the hook off.
+ * Process-wide; no GPU work. */
+void pdg_debug_fail_allocations(int n);
 
 void pdg_destroy(pdg_ctx* ctx);
 const char* pdg_status_string(pdg_status s);
@@ -207,17 +237,24 @@ pdg_status pdg_load_state(pdg_ctx* ctx, const void* host_buf, size_t n, void* cu
  * 6-neighbour graph Laplacian), computed by the same preconditioner kernels as
  * pdg_precondition, without a context and without allocating: its scratch lives in one
  * fixed file-scope device array of about 6.5 MB (two res^3 x 3 float buffers and the z-solve
- * pivot table at the maximum res, plus small tables), which every GPU that loads the library
- * keeps until the process exits.
- *  - g, out: DEVICE pointers to float [res^3][3] ((z*res + y)*res + x); host pointers give
- *    PDG_ERR_INVALID.  res: 1 or a power of two up to PDG_STATIC_MAX_RES; larger grids give
- *    PDG_ERR_BUDGET (use pdg_precondition).  lambda: finite, >= 0.
- *  - The first call on a device looks up the array's device address and sets the kernels'
- *    shared-memory limits; make that first call before any stream capture.
- *  - Every call uses the same array and leaves its contents behind (each call overwrites
- *    everything it reads).  Calls whose work overlaps on the GPU (other streams, threads or
- *    processes sharing the device) race on it: serialise them.
- *  - Asynchronous on `cuda_stream`; nothing is allocated, freed or synchronised. */
+ * pivot table at the maximum res, plus small tables and records), which every GPU that loads
+ * the library keeps until the process exits.
+ *  - g, out: DEVICE pointers of the current device to float [res^3][3] ((z*res + y)*res + x);
+ *    host pointers or another GPU's memory give PDG_ERR_INVALID.  The call cannot check
+ *    their length: each must hold res^3 * 3 floats.  res: 1 or a power of two up to
+ *    PDG_STATIC_MAX_RES; larger grids give PDG_ERR_BUDGET (use pdg_precondition).
+ *    lambda: finite, >= 0.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *    and sets the kernels' shared-memory limits; make that first call before any stream
+ *    capture.
+ *  - Every call uses the same array and leaves its contents behind; each call writes its
+ *    tables, job record and gradient copy before reading them, so nothing carries over.
+ *    Calls in one process whose work overlaps on the GPU (other streams or threads) race on
+ *    the array: serialise them.  (Each process has its own copy of the array.)
+ *  - Asynchronous on `cuda_stream`: every table and record is written by a kernel from its
+ *    launch arguments, so nothing is copied from host memory, allocated, freed or
+ *    synchronised.  A launch error left by earlier work on the calling thread is cleared on
+ *    entry, so the status returned is this call's. */
 #define PDG_STATIC_MAX_RES 64
 pdg_status pdg_precondition_static(int res, float lambda, const float* g, float* out, void* cuda_stream);
 

@@ -17,8 +17,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpdg.so")
 MAX_LEVELS = 8
 
+PAYLOAD_DISPLACEMENT, PAYLOAD_CAYLEY = 0, 1
 OK, ERR_INVALID, ERR_OOM, ERR_BUDGET, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE = range(8)
-BUF_THETA, BUF_GRAD, BUF_PGRAD, BUF_Y, BUF_POINT_GRAD, BUF_NN_FWD, BUF_NN_REV, BUF_LOSS, BUF_SOURCE = range(9)
+BUF_THETA, BUF_GRAD, BUF_PGRAD, BUF_Y, BUF_POINT_GRAD, BUF_NN_FWD, BUF_NN_REV, BUF_LOSS, BUF_SOURCE, BUF_COUNTERS = range(10)
+DEBUG_KEEP_PGRAD, DEBUG_COUNT_NN = 1, 2
 
 
 class pdg_config(C.Structure):
@@ -41,6 +43,7 @@ class pdg_config(C.Structure):
         ("precondition", C.c_int),
         ("robust_weight_stopgrad", C.c_int),
         ("warm_start", C.c_int),
+        ("payload", C.c_int),
     ]
 
 
@@ -52,6 +55,7 @@ class pdg_fit_stats(C.Structure):
         ("iso", C.c_double),
         ("n_steps", C.c_int),
         ("status", C.c_int),
+        ("nn_ties", C.c_int),
     ]
 
 
@@ -86,6 +90,7 @@ _SIGS = {
     "pdg_profile_step": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
     "pdg_step_kernel_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "pdg_destroy": (None, [C.c_void_p]),
+    "pdg_debug_fail_allocations": (None, [C.c_int]),
     "pdg_status_string": (C.c_char_p, [C.c_int]),
     "pdg_last_error": (C.c_char_p, [C.c_void_p]),
     "pdg_batch_create": (C.c_int, [C.c_int, C.POINTER(C.c_void_p)]),
@@ -178,6 +183,8 @@ def pdg_config_default(**overrides) -> pdg_config:
                 getattr(cfg, k)[i] = float(v[i])
         elif k in ("precondition", "robust_weight_stopgrad", "warm_start"):
             setattr(cfg, k, int(bool(v)))
+        elif k == "payload":
+            cfg.payload = {"displacement": PAYLOAD_DISPLACEMENT, "cayley": PAYLOAD_CAYLEY}.get(v, v)
         else:
             setattr(cfg, k, float(v))
     return cfg
@@ -249,7 +256,7 @@ def pdg_read(ctx, which: int, level: int, out, stream=None):
 
 
 def pdg_write_theta(ctx, level: int, theta, stream=None):
-    a = _Arr(theta, np.float32, 3, "theta")
+    a = _Arr(theta, np.float32, None, "theta")  # [res^3, C]; the library checks nothing else
     _check(load().pdg_write_theta(ctx, int(level), a.ptr, _stream(stream)), ctx)
 
 
@@ -268,16 +275,32 @@ def pdg_precondition(ctx, level: int, g, out, stream=None):
 
 
 def pdg_precondition_static(res: int, lam: float, g, out, stream=None):
-    """Allocation-free (I + lambda L)^{-2} on a res^3 grid; g and out must be CUDA tensors
-    of shape [res^3, 3].  Returns the status code (not raised: callers of this entry point
-    typically handle errors themselves)."""
+    """Allocation-free (I + lambda L)^{-2} on a res^3 grid; g and out must be float32 CUDA
+    tensors of shape [res^3, 3] on the current device (ValueError otherwise: the C entry
+    point cannot check a buffer's length).  Returns the status code of the call (not raised:
+    callers of this entry point typically handle errors themselves)."""
+    import torch
+
+    for name, t in (("g", g), ("out", out)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} must be on the current device cuda:{torch.cuda.current_device()}")
     a = _Arr(g, np.float32, 3, "g")
     o = _Arr(out, np.float32, 3, "out")
+    if res >= 1 and not (a.n == o.n == int(res) ** 3):
+        raise ValueError(f"g and out must hold res^3 = {int(res) ** 3} rows, got {a.n} and {o.n}")
     return int(load().pdg_precondition_static(int(res), float(lam), a.ptr, o.ptr, _stream(stream)))
 
 
-def pdg_set_debug(ctx, keep_pgrad: bool = True):
-    _check(load().pdg_set_debug(ctx, int(bool(keep_pgrad))), ctx)
+def pdg_set_debug(ctx, keep_pgrad: bool = True, count_nn: bool = False):
+    flags = (DEBUG_KEEP_PGRAD if keep_pgrad else 0) | (DEBUG_COUNT_NN if count_nn else 0)
+    _check(load().pdg_set_debug(ctx, flags), ctx)
+
+
+def pdg_debug_fail_allocations(n: int):
+    """Test hook: the library's next n device allocations fail (PDG_ERR_OOM)."""
+    load().pdg_debug_fail_allocations(int(n))
 
 
 def pdg_profile_stages() -> int:

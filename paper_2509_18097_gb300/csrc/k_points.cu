@@ -13,6 +13,9 @@ namespace pdg {
 __device__ __forceinline__ void job_bump(const Job& J, int bump) {
   *J.hard_count = 0;
   *J.gmax = 0u;
+  J.counters[CNT_NN_CANDIDATES] = 0ull;
+  J.counters[CNT_NN_TIES] = 0ull;
+  J.counters[CNT_NN_HARD] = 0ull;
   if (bump == 1) {
     const int k = *J.step + 1;
     *J.step = k;
@@ -33,6 +36,7 @@ __global__ void k_plan(Plan* P) {
     const int G = 1 << J->mov.bits;
     cnt[ST_Q][j] = J->Q;
     cnt[ST_NNQ][j] = J->Q + 2 * J->M;
+    cnt[ST_NNR][j] = 2 * J->M;
     cnt[ST_E][j] = J->E;
     cnt[ST_MOVCH][j] = (2 * G * G * G + SCAN_CHUNK - 1) / SCAN_CHUNK;
     int a = 0, t = 0, p3 = 0, cols = 0, ad = 0;
@@ -43,15 +47,16 @@ __global__ void k_plan(Plan* P) {
     int na_l[MAXL], ne_l[MAXL];
 #pragma unroll
     for (int l = 0; l < MAXL; ++l) na_l[l] = l < L ? *J->lev[l].n_active : 0;
+    // every point adds one term to each of its 8 interpolation corners (one for n = 1)
 #pragma unroll
-    for (int l = 0; l < MAXL; ++l) ne_l[l] = na_l[l] > 0 ? J->lev[l].act_ptr[na_l[l]] : 0;
+    for (int l = 0; l < MAXL; ++l) ne_l[l] = l < L ? (J->lev[l].n > 1 ? 8 : 1) * J->Q : 0;
 #pragma unroll
     for (int l = 0; l < MAXL; ++l) {
       if (l >= L) break;
-      // adjoint (in blocks of 8 warps): 2^adj_lg lanes per row, 8 to 16 entries per lane
-      // (a row holds one entry per point in the 8 cells around its vertex: a few dozen on
+      // adjoint (in blocks of 8 warps): 2^adj_lg lanes per row, 8 to 16 terms per lane
+      // (a row holds one term per point in the 8 cells around its vertex: a few dozen on
       // fine levels, thousands on coarse ones), so a warp sums 32 >> adj_lg rows; rows of
-      // 512 entries or more on average (adj_lg = 6) get a whole block each
+      // 512 terms or more on average (adj_lg = 6) get a whole block each
       Level& lv = J->lev[l];
       const int na = na_l[l];
       const int ne = ne_l[l];
@@ -64,13 +69,13 @@ __global__ void k_plan(Plan* P) {
       if (J->lev[l].n > 128) t += J->lev[l].tiles;
       else {
         p3 += J->lev[l].n;
-        cols += 3 * ((J->lev[l].n * J->lev[l].n + 63) / 64);  // blocks of 64 columns (two threads each)
+        cols += J->C * ((J->lev[l].n * J->lev[l].n + 63) / 64);  // blocks of 64 columns (two threads each)
         ad += (J->lev[l].n3 + 3) >> 2;
       }
     }
     cnt[ST_ADJ][j] = a + ((aw + 7) >> 3);
     cnt[ST_TILE][j] = t;
-    cnt[ST_PLANE][j] = 3 * p3;
+    cnt[ST_PLANE][j] = J->C * p3;
     cnt[ST_COL][j] = cols;
     cnt[ST_ADAM][j] = ad;
     cnt[ST_JOB][j] = 1;
@@ -90,41 +95,46 @@ __global__ void k_plan(Plan* P) {
 
 // ------------------------------------------------------------------------------ (a) eval
 
-// The 8 corner values of a point in one level and its fractional coordinates (Eq. 1;
-// vertex-aligned levels, coordinates clamped to the domain, last cell closed).  A level of
-// one vertex has the constant value c[0].
-struct LevelTap {
-  float4 c[8];
+// Trilinear interpolation of one level's values at a point (Eq. 1; vertex-aligned levels,
+// coordinates clamped to the domain, last cell closed): the cell's first vertex and the
+// fractional coordinates, computed once and used for each payload array of the level.  A
+// level of one vertex has the constant value v[0].
+struct LevelCoord {
+  int base;  // flat index of the cell's (0, 0, 0) corner
+  int n;
   float fx, fy, fz;
-  bool one;
 };
 
-__device__ __forceinline__ void level_tap(const Job& J, const Level& lv, float px, float py, float pz, LevelTap& T) {
-  const int n = lv.n;
-  T.one = n == 1;
-  if (T.one) {
-    T.c[0] = lv.theta[0];
-    T.fx = T.fy = T.fz = 0.f;
-    return;
+__device__ __forceinline__ LevelCoord level_coord(const Job& J, const Level& lv, float px, float py, float pz) {
+  LevelCoord c;
+  c.n = lv.n;
+  if (lv.n == 1) {
+    c.base = 0;
+    c.fx = c.fy = c.fz = 0.f;
+    return c;
   }
   int ix, iy, iz;
-  grid_coord(px, J.lo[0], lv.sc_hi[0], lv.sc_lo[0], n, ix, T.fx);
-  grid_coord(py, J.lo[1], lv.sc_hi[1], lv.sc_lo[1], n, iy, T.fy);
-  grid_coord(pz, J.lo[2], lv.sc_hi[2], lv.sc_lo[2], n, iz, T.fz);
-  const float4* t0 = lv.theta + ((size_t)(iz * n + iy) * n + ix);
-  const float4* t1 = t0 + (size_t)n * n;
-  T.c[0] = t0[0]; T.c[1] = t0[1]; T.c[2] = t0[n]; T.c[3] = t0[n + 1];
-  T.c[4] = t1[0]; T.c[5] = t1[1]; T.c[6] = t1[n]; T.c[7] = t1[n + 1];
+  grid_coord(px, J.lo[0], lv.sc_hi[0], lv.sc_lo[0], lv.n, ix, c.fx);
+  grid_coord(py, J.lo[1], lv.sc_hi[1], lv.sc_lo[1], lv.n, iy, c.fy);
+  grid_coord(pz, J.lo[2], lv.sc_hi[2], lv.sc_lo[2], lv.n, iz, c.fz);
+  c.base = (iz * lv.n + iy) * lv.n + ix;
+  return c;
 }
 
-__device__ __forceinline__ void level_add(const LevelTap& T, float& ux, float& uy, float& uz) {
-  if (T.one) {
-    ux += T.c[0].x; uy += T.c[0].y; uz += T.c[0].z;
+// adds sum_corners w * v[corner] to u (all 8 corner loads issued before any is used)
+__device__ __forceinline__ void level_add(const LevelCoord& L, const float4* __restrict__ v, float& ux, float& uy,
+                                          float& uz) {
+  if (L.n == 1) {
+    const float4 c = v[0];
+    ux += c.x; uy += c.y; uz += c.z;
     return;
   }
-  const float fx = T.fx, fy = T.fy, fz = T.fz;
-  const float4 c000 = T.c[0], c100 = T.c[1], c010 = T.c[2], c110 = T.c[3];
-  const float4 c001 = T.c[4], c101 = T.c[5], c011 = T.c[6], c111 = T.c[7];
+  const int n = L.n;
+  const float4* t0 = v + L.base;
+  const float4* t1 = t0 + (size_t)n * n;
+  const float4 c000 = t0[0], c100 = t0[1], c010 = t0[n], c110 = t0[n + 1];
+  const float4 c001 = t1[0], c101 = t1[1], c011 = t1[n], c111 = t1[n + 1];
+  const float fx = L.fx, fy = L.fy, fz = L.fz;
   const float gx = 1.f - fx, gy = 1.f - fy, gz = 1.f - fz;
   const float w000 = gx * gy * gz, w100 = fx * gy * gz, w010 = gx * fy * gz, w110 = fx * fy * gz;
   const float w001 = gx * gy * fz, w101 = fx * gy * fz, w011 = gx * fy * fz, w111 = fx * fy * fz;
@@ -136,33 +146,54 @@ __device__ __forceinline__ void level_add(const LevelTap& T, float& ux, float& u
         w011 * c011.z + w111 * c111.z;
 }
 
-// u(p) = (1/L) sum_l sum_{8 corners} w * theta_l[corner]   (Eq. 1), levels summed in order
-__device__ float3 eval_disp(const Job& J, float px, float py, float pz) {
-  float ux = 0.f, uy = 0.f, uz = 0.f;
+// The payload averaged over the levels at p (Eq. 1): a = the displacement (or z of the
+// Cayley payload), t = the Cayley translation (zero for the displacement payload)
+__device__ void eval_payload(const Job& J, float px, float py, float pz, float3& a, float3& t) {
+  float ax = 0.f, ay = 0.f, az = 0.f, tx = 0.f, ty = 0.f, tz = 0.f;
   for (int l = 0; l < J.L; ++l) {
-    LevelTap A;
-    level_tap(J, J.lev[l], px, py, pz, A);
-    level_add(A, ux, uy, uz);
+    const Level& lv = J.lev[l];
+    const LevelCoord c = level_coord(J, lv, px, py, pz);
+    level_add(c, lv.theta, ax, ay, az);
+    if (J.C == 6) level_add(c, lv.theta_t, tx, ty, tz);
   }
   const float invL = 1.f / (float)J.L;
-  return make_float3(ux * invL, uy * invL, uz * invL);
+  a = make_float3(ax * invL, ay * invL, az * invL);
+  t = make_float3(tx * invL, ty * invL, tz * invL);
+}
+
+// the deformed position of x (Sec. 3.3): x + u(x), or R(z(x)) x + t(x) with the Cayley
+// payload (then also z and u = (I - Z)^{-1} x for the backward)
+__device__ __forceinline__ float3 deform_point(const Job& J, float3 x, float3& z, float3& u) {
+  float3 a, t;
+  eval_payload(J, x.x, x.y, x.z, a, t);
+  if (J.C != 6) return make_float3(x.x + a.x, x.y + a.y, x.z + a.z);
+  z = a;
+  u = cayley_u(z, x);
+  return make_float3(2.f * u.x - x.x + t.x, 2.f * u.y - x.y + t.y, 2.f * u.z - x.z + t.z);
 }
 
 // y = x + u(x) on Q; the cell key of y in the moving grid (set 0: template, set 1: source)
 // and its count; clears the point's fixed-point reverse-Chamfer accumulator.  The thread of
-// a job's first point also starts the job's step (job_bump; bump 0: none).
+// a job's first point also starts the job's step (job_bump; bump 0: none).  Points are taken
+// in the finest level's cell order (the per-frame sort of the adjoint), so the lanes of a
+// warp interpolate between the same or neighbouring grid vertices.
 __global__ void k_interp(const Plan* __restrict__ P, int bump) {
   const int nj = P->n_jobs;
   const int total = P->pre[ST_Q][nj];
   for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
     const int j = find_job(P->pre[ST_Q], nj, it);
     const Job& J = *P->jobs[j];
-    const int p = it - P->pre[ST_Q][j];
+    const int p = __float_as_int(__ldg(&J.lev[J.L - 1].xs[it - P->pre[ST_Q][j]].w));
     if (bump && p == 0) job_bump(J, bump);
     const float4 x = J.x[p];
-    const float3 u = eval_disp(J, x.x, x.y, x.z);
-    const float4 y = make_float4(x.x + u.x, x.y + u.y, x.z + u.z, 0.f);
+    float3 z, u;
+    const float3 yy = deform_point(J, make_float3(x.x, x.y, x.z), z, u);
+    const float4 y = make_float4(yy.x, yy.y, yy.z, 0.f);
     J.y[p] = y;
+    if (J.C == 6) {
+      J.zq[p] = make_float4(z.x, z.y, z.z, 0.f);
+      J.uq[p] = make_float4(u.x, u.y, u.z, 0.f);
+    }
     const int key = cell_key(J.mov, y.x, y.y, y.z, p < J.V ? 0 : 1);
     J.mov.keys[p] = key;
     atomicAdd(&J.mov.hist[key], 1);
@@ -241,9 +272,18 @@ __global__ void k_assemble(const Plan* __restrict__ P) {
       g.z += J.w_iso * iz;
     }
     J.gy[p] = g;
-    // running bound on |dL/dy| of the job (order-independent max, one atomic per job per warp)
-    unsigned bits = __float_as_uint(fmaxf(fabsf(g.x), fmaxf(fabsf(g.y), fabsf(g.z))));
-    if (!(fmaxf(fabsf(g.x), fmaxf(fabsf(g.y), fabsf(g.z))) <= 3.0e38f)) bits = 0x7f800000u;
+    float gm = fmaxf(fabsf(g.x), fmaxf(fabsf(g.y), fabsf(g.z)));
+    if (J.C == 6) {  // the point's gradient with respect to its averaged Cayley z
+      const float4 z4 = J.zq[p], u4 = J.uq[p];
+      const float3 gzv = cayley_grad_z(make_float3(z4.x, z4.y, z4.z), make_float3(u4.x, u4.y, u4.z),
+                                       make_float3(g.x, g.y, g.z));
+      J.gz[p] = make_float4(gzv.x, gzv.y, gzv.z, 0.f);
+      gm = fmaxf(gm, fmaxf(fabsf(gzv.x), fmaxf(fabsf(gzv.y), fabsf(gzv.z))));
+    }
+    // running bound on the point gradients of the job (order-independent max, one atomic per
+    // job per warp); it sets the adjoint's fixed-point scale
+    unsigned bits = __float_as_uint(gm);
+    if (!(gm <= 3.0e38f)) bits = 0x7f800000u;
     const unsigned act = __activemask();
     const unsigned same = __match_any_sync(act, j);
     const unsigned m = __reduce_max_sync(same, bits);
@@ -382,23 +422,24 @@ __global__ void k_tgt_scatter(Job* J) {
   }
 }
 
-// frame end: X_t = X_{t-1} + u_t(X_{t-1}) with the final grids (Sec. 3.3)
+// frame end: X_t = M(T_t(X_{t-1})) X_{t-1} with the final grids (Sec. 3.3)
 __global__ void k_end_frame(Job* J) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < J->V; p += gridDim.x * blockDim.x) {
     const float4 x = J->x[p];
-    const float3 u = eval_disp(*J, x.x, x.y, x.z);
-    J->verts4[p] = make_float4(x.x + u.x, x.y + u.y, x.z + u.z, 0.f);
+    float3 z, u;
+    const float3 y = deform_point(*J, make_float3(x.x, x.y, x.z), z, u);
+    J->verts4[p] = make_float4(y.x, y.y, y.z, 0.f);
   }
 }
 
-// out = xyz + u(xyz) for arbitrary points ([n][3] float in/out, device)
+// the frame's deformation applied to arbitrary points ([n][3] float in/out, device)
 __global__ void k_deform(const Job* __restrict__ J, const float* __restrict__ in, float* __restrict__ out, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const float px = in[3 * i], py = in[3 * i + 1], pz = in[3 * i + 2];
-    const float3 u = eval_disp(*J, px, py, pz);
-    out[3 * i] = px + u.x;
-    out[3 * i + 1] = py + u.y;
-    out[3 * i + 2] = pz + u.z;
+    float3 z, u;
+    const float3 y = deform_point(*J, make_float3(in[3 * i], in[3 * i + 1], in[3 * i + 2]), z, u);
+    out[3 * i] = y.x;
+    out[3 * i + 1] = y.y;
+    out[3 * i + 2] = y.z;
   }
 }
 
@@ -433,28 +474,52 @@ void launch_deform(const Job* J, const float* in, float* out, int n, cudaStream_
   k_deform<<<blocks_for(n, 256), 256, 0, s>>>(J, in, out, n);
 }
 
-__global__ void k_soa_to_aos(const float* __restrict__ in, float* __restrict__ out, int n3) {
+// channel-planar [C][n3] <-> interleaved [n3][C]
+__global__ void k_soa_to_aos(const float* __restrict__ in, float* __restrict__ out, int n3, int C) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += gridDim.x * blockDim.x)
+    for (int c = 0; c < C; ++c) out[(size_t)C * i + c] = in[(size_t)c * n3 + i];
+}
+__global__ void k_aos_to_soa(const float* __restrict__ in, float* __restrict__ out, int n3, int C) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += gridDim.x * blockDim.x)
+    for (int c = 0; c < C; ++c) out[(size_t)c * n3 + i] = in[(size_t)C * i + c];
+}
+void launch_aos_to_soa(const float* in, float* out, int n3, cudaStream_t s, int C) {
+  k_aos_to_soa<<<blocks_for(n3, 256), 256, 0, s>>>(in, out, n3, C);
+}
+void launch_soa_to_aos(const float* in, float* out, int n3, cudaStream_t s, int C) {
+  k_soa_to_aos<<<blocks_for(n3, 256), 256, 0, s>>>(in, out, n3, C);
+}
+
+// level values [n3][C] <-> the float4 arrays of a level (theta; theta_t holds channels 3..5)
+__global__ void k_pack_theta(const float* __restrict__ in, float4* __restrict__ th, float4* __restrict__ tht, int n3,
+                             int C) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += gridDim.x * blockDim.x) {
-    out[3 * i] = in[i];
-    out[3 * i + 1] = in[n3 + i];
-    out[3 * i + 2] = in[2 * n3 + i];
+    const float* r = in + (size_t)C * i;
+    th[i] = make_float4(r[0], r[1], r[2], 0.f);
+    if (C == 6) tht[i] = make_float4(r[3], r[4], r[5], 0.f);
   }
 }
-__global__ void k_aos_to_soa(const float* __restrict__ in, float* __restrict__ out, int n3) {
+__global__ void k_unpack_theta(const float4* __restrict__ th, const float4* __restrict__ tht, float* __restrict__ out,
+                               int n3, int C) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += gridDim.x * blockDim.x) {
-    out[i] = in[3 * i];
-    out[n3 + i] = in[3 * i + 1];
-    out[2 * n3 + i] = in[3 * i + 2];
+    float* r = out + (size_t)C * i;
+    const float4 a = th[i];
+    r[0] = a.x; r[1] = a.y; r[2] = a.z;
+    if (C == 6) {
+      const float4 b = tht[i];
+      r[3] = b.x; r[4] = b.y; r[5] = b.z;
+    }
   }
 }
-void launch_aos_to_soa(const float* in, float* out, int n3, cudaStream_t s) {
-  k_aos_to_soa<<<blocks_for(n3, 256), 256, 0, s>>>(in, out, n3);
+void launch_pack_theta(const float* in, float4* th, float4* tht, int n3, int C, cudaStream_t s) {
+  k_pack_theta<<<blocks_for(n3, 256), 256, 0, s>>>(in, th, tht, n3, C);
 }
+void launch_unpack_theta(const float4* th, const float4* tht, float* out, int n3, int C, cudaStream_t s) {
+  k_unpack_theta<<<blocks_for(n3, 256), 256, 0, s>>>(th, tht, out, n3, C);
+}
+
 __global__ void k_copy_int(const int* __restrict__ in, int* __restrict__ out, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = in[i];
-}
-void launch_soa_to_aos(const float* in, float* out, int n3, cudaStream_t s) {
-  k_soa_to_aos<<<blocks_for(n3, 256), 256, 0, s>>>(in, out, n3);
 }
 void launch_aos_to_float4(const float* in, float4* out, int n, cudaStream_t s) { launch_pack4(in, out, n, s); }
 void launch_copy_int(const int* in, int* out, int n, cudaStream_t s) {

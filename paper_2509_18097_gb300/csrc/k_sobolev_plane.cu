@@ -255,17 +255,17 @@ __device__ __forceinline__ void dct3_pre(const float2 (&X)[N2], int t, int lbase
   }
 }
 
-// maps a plane item of a job to (level, index); 3n items per level (plane major, then
+// maps a plane item of a job to (level, index); C n items per level (plane major, then
 // channel), only levels with n <= 128 take part
 __device__ __forceinline__ bool plane_item(const Job& J, int r, int& l, int& idx) {
   for (l = 0; l < J.L; ++l) {
     const int n = J.lev[l].n;
     if (n > 128) continue;
-    if (r < 3 * n) {
+    if (r < J.C * n) {
       idx = r;
       return true;
     }
-    r -= 3 * n;
+    r -= J.C * n;
   }
   return false;
 }
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(PL_THREADS, 2) k_sobp(const Plan* __restrict__
     if (!plane_item(J, it - P->pre[ST_PLANE][j], l, idx)) continue;
     const Level& lv = J.lev[l];
     const int n = lv.n, n3 = lv.n3;
-    const int q = idx / 3, c = idx - 3 * q;  // z-plane, channel
+    const int q = idx / J.C, c = idx - J.C * q;  // z-plane, channel
     if (n == 1) {  // no transform: copy g to tmp (the scale is 1)
       if (threadIdx.x == 0) lv.tmp[c] = lv.g[c];
       continue;
@@ -466,12 +466,12 @@ __device__ __forceinline__ bool column_item(const Job& J, int r, int& l, int& c,
     const int n = J.lev[l].n;
     if (n > 128) continue;
     const int per = (n * n + COLS_PER_ITEM - 1) / COLS_PER_ITEM;
-    if (r < 3 * per) {
+    if (r < J.C * per) {
       c = r / per;
       col0 = (r - c * per) * COLS_PER_ITEM;
       return true;
     }
-    r -= 3 * per;
+    r -= J.C * per;
   }
   return false;
 }
@@ -607,7 +607,7 @@ __global__ void __launch_bounds__(PL_THREADS, 2) k_sobp_inv(const Plan* __restri
     if (!plane_item(J, it - P->pre[ST_PLANE][j], l, idx)) continue;
     const Level& lv = J.lev[l];
     const int n = lv.n;
-    const int q = idx / 3, c = idx - 3 * q;
+    const int q = idx / J.C, c = idx - J.C * q;
     if (n == 1) continue;  // tmp already holds the preconditioned gradient (the operator is 1)
     float* plane = smem;
     float2* scr = reinterpret_cast<float2*>(smem + ((plane_floats(n) + 1) & ~1));
@@ -642,6 +642,43 @@ __device__ __forceinline__ bool adam_item(const Job& J, int r, int& l, int& q) {
   return false;
 }
 
+// Adam on one channel of 4 consecutive vertices e .. e + 3: th[k] is channel c of vertex e + k
+__device__ __forceinline__ void adam4(const float* __restrict__ gsrc, float* __restrict__ m, float* __restrict__ v,
+                                      size_t off, float b1, float b2, float eps, float step, float ib2, float (&th)[4]) {
+  const float4 g4 = *reinterpret_cast<const float4*>(gsrc + off);
+  float4 m4 = *reinterpret_cast<const float4*>(m + off);
+  float4 v4 = *reinterpret_cast<const float4*>(v + off);
+  const float g[4] = {g4.x, g4.y, g4.z, g4.w};
+  float* mm = &m4.x;
+  float* vv = &v4.x;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    mm[k] = b1 * mm[k] + (1.f - b1) * g[k];
+    vv[k] = b2 * vv[k] + (1.f - b2) * g[k] * g[k];
+    th[k] -= step * mm[k] / (sqrtf(vv[k]) * ib2 + eps);
+  }
+  *reinterpret_cast<float4*>(m + off) = m4;
+  *reinterpret_cast<float4*>(v + off) = v4;
+}
+
+// Adam on the float4 array `t` (3 channels starting at channel c0 of the planar arrays)
+__device__ __forceinline__ void adam_float4(float4* __restrict__ t, const float* __restrict__ gsrc, float* m, float* v,
+                                            size_t n3, int c0, size_t e, float b1, float b2, float eps, float step,
+                                            float ib2) {
+  float4 th[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) th[k] = t[e + k];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float tc[4] = {(&th[0].x)[c], (&th[1].x)[c], (&th[2].x)[c], (&th[3].x)[c]};
+    adam4(gsrc, m, v, (size_t)(c0 + c) * n3 + e, b1, b2, eps, step, ib2, tc);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) (&th[k].x)[c] = tc[k];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) t[e + k] = th[k];
+}
+
 __global__ void __launch_bounds__(256) k_adam(const Plan* __restrict__ P) {
   const int nj = P->n_jobs;
   const int total = P->pre[ST_ADAM][nj];
@@ -659,39 +696,23 @@ __global__ void __launch_bounds__(256) k_adam(const Plan* __restrict__ P) {
     const float ib2 = J.bias[1];
     if (n3 >= 4) {
       const size_t e = (size_t)q << 2;
-      float4 th[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) th[k] = lv.theta[e + k];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const float4 g4 = *reinterpret_cast<const float4*>(gsrc + c * n3 + e);
-        float4 m4 = *reinterpret_cast<const float4*>(lv.m + c * n3 + e);
-        float4 v4 = *reinterpret_cast<const float4*>(lv.v + c * n3 + e);
-        const float g[4] = {g4.x, g4.y, g4.z, g4.w};
-        float* mm = &m4.x;
-        float* vv = &v4.x;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          mm[k] = b1 * mm[k] + (1.f - b1) * g[k];
-          vv[k] = b2 * vv[k] + (1.f - b2) * g[k] * g[k];
-          (&th[k].x)[c] -= step * mm[k] / (sqrtf(vv[k]) * ib2 + eps);
-        }
-        *reinterpret_cast<float4*>(lv.m + c * n3 + e) = m4;
-        *reinterpret_cast<float4*>(lv.v + c * n3 + e) = v4;
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) lv.theta[e + k] = th[k];
+      adam_float4(lv.theta, gsrc, lv.m, lv.v, n3, 0, e, b1, b2, eps, step, ib2);
+      if (J.C == 6) adam_float4(lv.theta_t, gsrc, lv.m, lv.v, n3, 3, e, b1, b2, eps, step, ib2);
     } else {  // n == 1
-      float4 th = lv.theta[0];
-      for (int c = 0; c < 3; ++c) {
-        const float g = gsrc[c * n3];
-        float m = b1 * lv.m[c * n3] + (1.f - b1) * g;
-        float v = b2 * lv.v[c * n3] + (1.f - b2) * g * g;
-        lv.m[c * n3] = m;
-        lv.v[c * n3] = v;
-        (&th.x)[c] -= step * m / (sqrtf(v) * ib2 + eps);
+      for (int half = 0; half < J.C / 3; ++half) {
+        float4* t = half ? lv.theta_t : lv.theta;
+        float4 th = t[0];
+        for (int c = 0; c < 3; ++c) {
+          const int cc = 3 * half + c;
+          const float g = gsrc[cc * n3];
+          float m = b1 * lv.m[cc * n3] + (1.f - b1) * g;
+          float v = b2 * lv.v[cc * n3] + (1.f - b2) * g * g;
+          lv.m[cc * n3] = m;
+          lv.v[cc * n3] = v;
+          (&th.x)[c] -= step * m / (sqrtf(v) * ib2 + eps);
+        }
+        t[0] = th;
       }
-      lv.theta[0] = th;
     }
   }
 }

@@ -7,8 +7,6 @@
 // a context (its arena) and a temporary buffer; this entry point instead keeps all of its
 // scratch in one file-scope device array of fixed size, which every GPU that loads the
 // library holds until the process exits.
-#include <cmath>
-#include <cstring>
 #include <mutex>
 
 #include "kernels.h"
@@ -63,15 +61,71 @@ unsigned char* scratch_address(pdg_status* st) {
   return g_scratch_addr[dev];
 }
 
-bool on_device(const void* p) {
+// Device memory (or managed memory) of the current device: a pointer into another GPU's
+// memory would need peer access, which this entry point does not set up.
+bool on_current_device(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return false;
+  int dev = -1;
+  return cudaGetDevice(&dev) == cudaSuccess && (a.type == cudaMemoryTypeManaged || a.device == dev);
 }
 }  // namespace
+
+// Writes the level's tables (path-Laplacian eigenvalues, FFT and DCT twiddles), the
+// one-level job that stops at the preconditioned gradient, and its plan into the scratch
+// array.  Everything comes in as kernel arguments, so the call copies nothing from host
+// memory.  One block.
+__global__ void k_static_setup(unsigned char* base, int n, int lg, float lam) {
+  float* mu = reinterpret_cast<float*>(base + SO_MU);
+  float2* tw = reinterpret_cast<float2*>(base + SO_TW);
+  float2* tw4 = reinterpret_cast<float2*>(base + SO_TW4);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    double sh, ch, s2, c2;
+    sincospi((double)k / (2.0 * n), &sh, &ch);  // angle pi k / 2n
+    sincospi(2.0 * k / n, &s2, &c2);            // angle 2 pi k / n
+    mu[k] = (float)(4.0 * sh * sh);
+    tw[k] = make_float2((float)c2, (float)-s2);
+    tw4[k] = make_float2((float)ch, (float)-sh);
+  }
+  // zero the job and plan records word by word, then fill the fields that matter
+  unsigned* jw = reinterpret_cast<unsigned*>(base + SO_JOB);
+  for (size_t i = threadIdx.x; i < sizeof(Job) / 4; i += blockDim.x) jw[i] = 0u;
+  unsigned* pw = reinterpret_cast<unsigned*>(base + SO_PLAN);
+  for (size_t i = threadIdx.x; i < sizeof(Plan) / 4; i += blockDim.x) pw[i] = 0u;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Job& J = *reinterpret_cast<Job*>(base + SO_JOB);
+    J.L = 1;
+    J.C = 3;
+    J.precondition = 1;
+    J.keep_pgrad = 1;
+    J.no_adam = 1;
+    Level& lv = J.lev[0];
+    lv.n = n;
+    lv.lg = lg;
+    lv.n3 = n * n * n;
+    lv.tiles = (n * n + TILE_LINES - 1) / TILE_LINES;
+    lv.lam = lam;
+    lv.g = reinterpret_cast<float*>(base + SO_G);
+    lv.tmp = reinterpret_cast<float*>(base + SO_TMP);
+    lv.piv = reinterpret_cast<float*>(base + SO_PIV);
+    lv.piv_slow = reinterpret_cast<int*>(base + SO_SLOW);
+    lv.mu = mu;
+    lv.tw = tw;
+    lv.tw4 = tw4;
+    lv.n_active = reinterpret_cast<int*>(base + SO_NA);
+    *lv.n_active = 0;
+    J.bias = reinterpret_cast<float*>(base + SO_BIAS);
+    J.bias[0] = J.bias[1] = 1.f;
+    Plan& P = *reinterpret_cast<Plan*>(base + SO_PLAN);
+    P.n_jobs = 1;
+    P.jobs[0] = &J;
+  }
+}
 
 }  // namespace pdg
 
@@ -82,75 +136,32 @@ extern "C" pdg_status pdg_precondition_static(int res, float lambda, const float
   if (!g || !out || !(lambda >= 0.f) || !(lambda < 3.0e38f)) return PDG_ERR_INVALID;
   if (res < 1 || (res & (res - 1)) != 0) return PDG_ERR_INVALID;
   if (res > STATIC_MAX_RES) return PDG_ERR_BUDGET;
-  if (!on_device(g) || !on_device(out)) return PDG_ERR_INVALID;
+  if (!on_current_device(g) || !on_current_device(out)) return PDG_ERR_INVALID;
+  // a launch error left behind by earlier, unrelated work would otherwise be reported as
+  // this call's
+  cudaGetLastError();
   pdg_status st = PDG_OK;
   unsigned char* base = scratch_address(&st);
   if (st != PDG_OK) return st;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const int n = res;
   const int n3 = n * n * n;
-  // one-level job that stops at the preconditioned gradient (Adam is skipped)
-  Job J;
-  std::memset(&J, 0, sizeof(J));
-  J.L = 1;
-  J.precondition = 1;
-  J.keep_pgrad = 1;
-  J.no_adam = 1;
-  Level& lv = J.lev[0];
-  lv.n = n;
   int lg = 0;
   while ((1 << lg) < n) ++lg;
-  lv.lg = lg;
-  lv.n3 = n3;
-  lv.tiles = (n * n + TILE_LINES - 1) / TILE_LINES;
-  lv.lam = lambda;
-  lv.g = reinterpret_cast<float*>(base + SO_G);
-  lv.tmp = reinterpret_cast<float*>(base + SO_TMP);
-  lv.piv = reinterpret_cast<float*>(base + SO_PIV);
-  lv.piv_slow = reinterpret_cast<int*>(base + SO_SLOW);
-  lv.mu = reinterpret_cast<float*>(base + SO_MU);
-  lv.tw = reinterpret_cast<float2*>(base + SO_TW);
-  lv.tw4 = reinterpret_cast<float2*>(base + SO_TW4);
-  lv.n_active = reinterpret_cast<int*>(base + SO_NA);
-  J.bias = reinterpret_cast<float*>(base + SO_BIAS);
-  Plan P;
-  std::memset(&P, 0, sizeof(P));
-  P.n_jobs = 1;
-  P.jobs[0] = reinterpret_cast<Job*>(base + SO_JOB);
-  // tables and structs in one host block (pageable copies are staged before the call returns)
-  struct Tables {
-    float mu[STATIC_MAX_RES];
-    float2 tw[STATIC_MAX_RES];
-    float2 tw4[STATIC_MAX_RES];
-    int n_active;
-    float bias[2];
-  } T;
-  const double PI = 3.14159265358979323846;
-  for (int k = 0; k < n; ++k) {
-    const double sk = std::sin(PI * k / (2.0 * n));
-    T.mu[k] = (float)(4.0 * sk * sk);
-    T.tw[k] = make_float2((float)std::cos(2 * PI * k / n), (float)-std::sin(2 * PI * k / n));
-    T.tw4[k] = make_float2((float)std::cos(PI * k / (2.0 * n)), (float)-std::sin(PI * k / (2.0 * n)));
-  }
-  T.n_active = 0;
-  T.bias[0] = T.bias[1] = 1.f;
-  if (cudaMemcpyAsync(lv.mu, T.mu, sizeof(float) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(lv.tw, T.tw, sizeof(float2) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(lv.tw4, T.tw4, sizeof(float2) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(lv.n_active, &T.n_active, sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(J.bias, T.bias, 2 * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(P.jobs[0], &J, sizeof(Job), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(base + SO_PLAN, &P, sizeof(Plan), cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return PDG_ERR_CUDA;
-  launch_sobz_pivots(lv.piv, lv.piv_slow, lv.mu, n, lambda, s);
-  const Plan* dP = reinterpret_cast<const Plan*>(base + SO_PLAN);
-  launch_aos_to_soa(g, lv.g, n3, s);
-  launch_plan(const_cast<Plan*>(dP), s);
+  k_static_setup<<<1, 256, 0, s>>>(base, n, lg, lambda);
+  float* lv_g = reinterpret_cast<float*>(base + SO_G);
+  float* lv_tmp = reinterpret_cast<float*>(base + SO_TMP);
+  launch_sobz_pivots(reinterpret_cast<float*>(base + SO_PIV), reinterpret_cast<int*>(base + SO_SLOW),
+                     reinterpret_cast<const float*>(base + SO_MU), n, lambda, s);
+  Plan* dP = reinterpret_cast<Plan*>(base + SO_PLAN);
+  launch_aos_to_soa(g, lv_g, n3, s);
+  launch_plan(dP, s);
   int sms = 1, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int per_sm = (227 * 1024) / plane_smem_max(n) < 8 ? (227 * 1024) / plane_smem_max(n) : 8;
   launch_sobolev_plane(dP, sms * (per_sm > 0 ? per_sm : 1), n, s);
-  launch_soa_to_aos(lv.tmp, out, n3, s);
+  launch_soa_to_aos(lv_tmp, out, n3, s);
   return cudaGetLastError() == cudaSuccess ? PDG_OK : PDG_ERR_CUDA;
 }
+

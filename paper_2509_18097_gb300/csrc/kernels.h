@@ -9,7 +9,7 @@ void launch_plan(Plan* P, cudaStream_t s);
 void launch_interp(const Plan* P, int grid, cudaStream_t s, int bump);
 void launch_mov_scan(const Plan* P, int grid, cudaStream_t s);
 void launch_mov_scatter(const Plan* P, int grid, cudaStream_t s);
-void launch_nn(const Plan* P, int grid, cudaStream_t s);
+void launch_nn(const Plan* P, int grid, cudaStream_t s, int mode);  // 1: forward queries, 2: reverse
 void launch_nn_hard(const Plan* P, int grid, cudaStream_t s);
 void launch_iso_edges(const Plan* P, int grid, cudaStream_t s);
 void launch_assemble(const Plan* P, int grid, cudaStream_t s);
@@ -43,12 +43,14 @@ void sobolev_configure();
 void sobolev_plane_configure();
 int plane_smem_bytes(int n);
 int plane_smem_max(int nmax);
-void launch_aos_to_soa(const float* in, float* out, int n3, cudaStream_t s);
+void launch_aos_to_soa(const float* in, float* out, int n3, cudaStream_t s, int C = 3);
 void launch_zmask(Job* J, const Job& hJ, cudaStream_t s);
 void launch_sobz_pivots(float* piv, int* slow, const float* mu, int n, float lam, cudaStream_t s);
 
 // misc conversions
-void launch_soa_to_aos(const float* in, float* out, int n3, cudaStream_t s);
+void launch_soa_to_aos(const float* in, float* out, int n3, cudaStream_t s, int C = 3);
+void launch_pack_theta(const float* in, float4* th, float4* tht, int n3, int C, cudaStream_t s);
+void launch_unpack_theta(const float4* th, const float4* tht, float* out, int n3, int C, cudaStream_t s);
 void launch_aos_to_float4(const float* in, float4* out, int n, cudaStream_t s);
 void launch_copy_int(const int* in, int* out, int n, cudaStream_t s);
 

@@ -46,24 +46,27 @@ struct Level {
   float sc_hi[3], sc_lo[3];  // (n - 1) / (hi - lo) per axis as a float pair (hi + lo)
   float lr;    // learning rate of the level (already x0.1 without preconditioning)
   float lam;   // lambda of the level
-  float4* theta;  // [n3] values (x, y, z, 0)
-  float* m;       // [3][n3] Adam first moment
-  float* v;       // [3][n3] Adam second moment
-  float* g;       // [3][n3] dLoss/dTheta (zero at vertices no point touches)
-  float* tmp;     // [3][n3] spectral work array (and preconditioned gradient in debug mode)
+  float4* theta;  // [n3] values (x, y, z, 0): the displacement, or z of the Cayley payload
+  float4* theta_t;  // [n3] translation t of the Cayley payload (null for the displacement payload)
+  float* m;       // [C][n3] Adam first moment (channel-planar; C = 3, or 6: z then t)
+  float* v;       // [C][n3] Adam second moment
+  float* g;       // [C][n3] dLoss/dTheta (zero at vertices no point touches)
+  float* tmp;     // [C][n3] spectral work array (and preconditioned gradient in debug mode)
   int* zmask;     // [n] 1 for z-planes that hold an active vertex (per frame); null: all planes
   float* piv;     // [(n/2 + 1) n^2] pivots of the z-direction twisted solves (n <= 128), per context
   int* piv_slow;  // device flag: some pivot past the first 16 differs from the limit (no register path)
   float* mu;      // [n] eigenvalues 4 sin^2(pi k / 2n) of the 1-D path Laplacian
   float2* tw;     // [n] FFT twiddles exp(-2 pi i k / n)
   float2* tw4;    // [n] DCT twiddles exp(-i pi k / 2n)
-  // point -> vertex interpolation lists, built once per frame (x is fixed in a frame)
-  int* cnt;       // [n3] per-vertex entry counts (zero between builds)
-  int* rowptr;    // [n3 + 1]
-  int* flag;      // [n3 + 1] active-vertex flags, then their exclusive prefix
+  // the query points sorted by the level's cell, built once per frame (x is fixed in a frame):
+  // cell c = (iz (n-1) + iy) (n-1) + ix holds the points whose interpolation cell it is
+  // (n = 1: one cell holding every point)
+  int* ccnt;      // [cells] points per cell (zero between builds)
+  int* coff;      // [cells + 1] exclusive prefix of ccnt
+  int* ckey;      // [Q] cell of each point (scratch of the build)
+  float4* xs;     // [Q] points in cell order: (fx, fy, fz, point index bits), f the in-cell fraction
+  int* flag;      // [n3 + 1] active-vertex flags (corner of a non-empty cell), then their prefix
   int* act_v;     // [cap] active vertices (ascending)
-  int* act_ptr;   // [cap + 1] entry range of each active vertex
-  int2* ent;      // [8 Q] entries: (point, bits of the trilinear weight / L)
   int* n_active;  // device scalar
   int* csum;      // scan scratch
   int adj_lg;     // adjoint: log2 of the lanes per row, 6 = a block per row (set by the plan kernel)
@@ -71,6 +74,7 @@ struct Level {
 
 struct Job {
   int L;
+  int C;                   // channels of the payload: 3 (displacement) or 6 (Cayley z, t)
   Level lev[MAXL];
   float lo[3], hi[3];
   float alpha, w_mesh, w_pts, w_iso;
@@ -83,7 +87,10 @@ struct Job {
   float4* y;               // [Q] deformed points
   float4* gfwd;            // [Q] forward Chamfer gradient
   long long* acc;          // [Q][3] reverse Chamfer sums, fixed point (2^-40)
-  float4* gy;              // [Q] dLoss/dy
+  float4* gy;              // [Q] dLoss/dy (= dLoss/dt with the Cayley payload)
+  float4* zq;              // [Q] Cayley payload: the point's averaged z (null otherwise)
+  float4* uq;              // [Q] Cayley payload: u = (I - Z)^{-1} x, so that R(z) x = 2 u - x
+  float4* gz;              // [Q] Cayley payload: dLoss/dz of the point
   float* loss_fwd;         // [Q] phi(d^2) of each forward query
   float* loss_rev;         // [2 max_pts] phi(d^2) of each reverse query (set 0 then set 1)
   float* loss_iso;         // [E] |r_e|
@@ -107,9 +114,15 @@ struct Job {
   float* bias;             // [2] 1 / (1 - beta1^k), 1 / sqrt(1 - beta2^k) of the current step
   double* loss;            // [4] total, cd_mesh, cd_pts, iso of the last step
   int* status;             // sticky error flags (1: non-finite loss)
+  unsigned long long* counters;  // [4] of the last step: NN candidates evaluated (counted only
+                                 // when count_nn), NN queries decided by an exact tie,
+                                 // queries left to the warp pass, reserved
+  int count_nn;            // 1: k_nn / k_nn_hard add their candidate counts to counters[0]
 };
 
-enum Stage { ST_Q = 0, ST_NNQ, ST_E, ST_MOVCH, ST_ADJ, ST_TILE, ST_JOB, ST_LOSSCH, ST_PLANE, ST_COL, ST_ADAM, NSTAGE };
+enum Counter { CNT_NN_CANDIDATES = 0, CNT_NN_TIES = 1, CNT_NN_HARD = 2 };
+
+enum Stage { ST_Q = 0, ST_NNQ, ST_NNR, ST_E, ST_MOVCH, ST_ADJ, ST_TILE, ST_JOB, ST_LOSSCH, ST_PLANE, ST_COL, ST_ADAM, NSTAGE };
 
 struct Plan {
   int n_jobs;
@@ -203,6 +216,31 @@ __device__ __forceinline__ void grid_coord(float x, float lo, float s_hi, float 
   }
   i0 = i;
   f = fminf(fmaxf(fr, 0.f), 1.f);
+}
+
+// The Cayley rotation of Sec. 3.3 applied to x without forming R(z) = (I + Z)(I - Z)^{-1}:
+// (I - Z)^{-1} = (I + Z + z z^T) / (1 + |z|^2) (multiply out with Z^2 = z z^T - |z|^2 I), and
+// R = 2 (I - Z)^{-1} - I, so R(z) x = 2 u - x with u = (x + z x x + z (z . x)) / (1 + |z|^2).
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+__device__ __forceinline__ float3 cayley_u(float3 z, float3 x) {
+  const float s = 1.f / (1.f + (z.x * z.x + z.y * z.y + z.z * z.z));
+  const float zx = z.x * x.x + z.y * x.y + z.z * x.z;
+  const float3 c = cross3(z, x);
+  return make_float3((x.x + c.x + z.x * zx) * s, (x.y + c.y + z.y * zx) * s, (x.z + c.z + z.z * zx) * s);
+}
+
+// dLoss/dz for y = R(z) x + t and g = dLoss/dy: d(R x) = 2 (I - Z)^{-1} dZ u = -2 (I - Z)^{-1} [u]x dz,
+// so dLoss/dz = 2 u x w with w = (I - Z)^{-T} g = (I + Z)^{-1} g = (g - z x g + z (z . g)) / (1 + |z|^2).
+__device__ __forceinline__ float3 cayley_grad_z(float3 z, float3 u, float3 g) {
+  const float s = 1.f / (1.f + (z.x * z.x + z.y * z.y + z.z * z.z));
+  const float zg = z.x * g.x + z.y * g.y + z.z * g.z;
+  const float3 c = cross3(z, g);
+  const float3 w = make_float3((g.x - c.x + z.x * zg) * s, (g.y - c.y + z.y * zg) * s, (g.z - c.z + z.z * zg) * s);
+  const float3 r = cross3(u, w);
+  return make_float3(2.f * r.x, 2.f * r.y, 2.f * r.z);
 }
 
 __device__ __forceinline__ long long to_fx(float v) { return __float2ll_rn(v * 1099511627776.0f); }

@@ -2,6 +2,7 @@
 // per-frame set-up, the CUDA-graph step, batching of contexts into one graph, and
 // checkpoint/resume.  See include/pdg.h for the contract of every entry point.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -41,6 +42,19 @@ int ilog2(int n) {
   int l = 0;
   while ((1 << l) < n) ++l;
   return l;
+}
+
+// Test hook: the next `g_fail_allocs` device allocations of the library report failure.
+std::atomic<int> g_fail_allocs{0};
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  int n = g_fail_allocs.load();
+  while (n > 0)
+    if (g_fail_allocs.compare_exchange_weak(n, n - 1)) {
+      *p = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+  return cudaMalloc(p, bytes);
 }
 
 bool is_device_ptr(const void* p) {
@@ -121,13 +135,14 @@ struct Layout {
   size_t total = 0;
   size_t job, plan, flag, stage, op_job, op_plan;
   struct Lv {
-    size_t theta, m, v, g, tmp, zmask, piv, piv_slow, mu, tw, tw4, cnt, rowptr, flag, act_v, act_ptr, ent, n_active, csum;
+    size_t theta, theta_t, m, v, g, tmp, zmask, piv, piv_slow, mu, tw, tw4, ccnt, coff, ckey, xs, flag, act_v, n_active,
+        csum;
     int cap;
   } lv[MAXL];
-  size_t x, y, gfwd, gy, acc, loss_fwd, loss_rev, loss_iso, nn_fwd, nn_rev, edge_d, edges, e_prev, v2e_ptr, v2e;
+  size_t x, y, gfwd, gy, zq, uq, gz, acc, loss_fwd, loss_rev, loss_iso, nn_fwd, nn_rev, edge_d, edges, e_prev, v2e_ptr, v2e;
   size_t src4, tgt4, verts4;
   size_t t_hist, t_off, t_keys, t_pts, t_csum, m_hist, m_off, m_keys, m_pts, m_csum;
-  size_t hard, hard_count, step, bias, loss, status, loss_part, gmax;
+  size_t hard, hard_count, step, bias, loss, status, loss_part, gmax, counters;
   int tbits, mbits;
 };
 
@@ -135,6 +150,7 @@ Layout make_layout(const pdg_config& c, int V, int E, int max_pts) {
   Layout L;
   Arena a;
   const int Q = V + max_pts;
+  const size_t C = c.payload == PDG_PAYLOAD_CAYLEY ? 6 : 3;
   L.job = a.take<Job>(1);
   L.plan = a.take<Plan>(1);
   L.op_job = a.take<Job>(1);
@@ -147,22 +163,24 @@ Layout make_layout(const pdg_config& c, int V, int E, int max_pts) {
     auto& v = L.lv[l];
     v.cap = (int)std::min<size_t>(n3, 8 * (size_t)Q);
     v.theta = a.take<float4>(n3);
-    v.m = a.take<float>(3 * n3);
-    v.v = a.take<float>(3 * n3);
-    v.g = a.take<float>(3 * n3);
-    v.tmp = a.take<float>(3 * n3);
+    v.theta_t = a.take<float4>(C == 6 ? n3 : 1);
+    v.m = a.take<float>(C * n3);
+    v.v = a.take<float>(C * n3);
+    v.g = a.take<float>(C * n3);
+    v.tmp = a.take<float>(C * n3);
     v.zmask = a.take<int>(n);
     v.piv = a.take<float>(n <= 128 ? (n / 2 + 1) * n * n : 1);
     v.piv_slow = a.take<int>(1);
     v.mu = a.take<float>(n);
     v.tw = a.take<float2>(n);
     v.tw4 = a.take<float2>(n);
-    v.cnt = a.take<int>(n3);
-    v.rowptr = a.take<int>(n3 + 1);
+    const size_t cells = n > 1 ? (n - 1) * (n - 1) * (n - 1) : 1;
+    v.ccnt = a.take<int>(cells);
+    v.coff = a.take<int>(cells + 1);
+    v.ckey = a.take<int>(Q);
+    v.xs = a.take<float4>(Q);
     v.flag = a.take<int>(n3 + 1);
     v.act_v = a.take<int>(v.cap);
-    v.act_ptr = a.take<int>(v.cap + 1);
-    v.ent = a.take<int2>(8 * (size_t)Q);
     v.n_active = a.take<int>(1);
     v.csum = a.take<int>((n3 + 1) / SCAN_CHUNK + 2);
   }
@@ -170,6 +188,9 @@ Layout make_layout(const pdg_config& c, int V, int E, int max_pts) {
   L.y = a.take<float4>(Q);
   L.gfwd = a.take<float4>(Q);
   L.gy = a.take<float4>(Q);
+  L.zq = a.take<float4>(C == 6 ? Q : 1);
+  L.uq = a.take<float4>(C == 6 ? Q : 1);
+  L.gz = a.take<float4>(C == 6 ? Q : 1);
   L.acc = a.take<long long>(3 * (size_t)Q);
   L.loss_fwd = a.take<float>(Q);
   L.loss_rev = a.take<float>(2 * (size_t)max_pts);
@@ -209,6 +230,7 @@ Layout make_layout(const pdg_config& c, int V, int E, int max_pts) {
   L.loss = a.take<double>(4);
   L.status = a.take<int>(1);
   L.gmax = a.take<unsigned>(1);
+  L.counters = a.take<unsigned long long>(4);
   L.total = (a.off + 255) & ~size_t(255);
   return L;
 }
@@ -218,6 +240,10 @@ const char* check_config(const pdg_config* c) {
   if (c->n_levels < 1 || c->n_levels > PDG_MAX_LEVELS) return "n_levels must be in 1..8";
   for (int l = 0; l < c->n_levels; ++l)
     if (!valid_res(c->res[l])) return "each res must be 1 or a power of two in 2..256";
+  if (c->payload != PDG_PAYLOAD_DISPLACEMENT && c->payload != PDG_PAYLOAD_CAYLEY) return "unknown payload";
+  if (c->payload == PDG_PAYLOAD_CAYLEY)
+    for (int l = 0; l < c->n_levels; ++l)
+      if (c->res[l] > 128) return "the Cayley payload takes levels of at most 128 vertices per axis";
   for (int a = 0; a < 3; ++a)
     if (!(std::isfinite(c->lo[a]) && std::isfinite(c->hi[a]) && c->hi[a] > c->lo[a])) return "domain must have lo < hi";
   const float f[] = {c->alpha, c->w_chamfer_mesh, c->w_chamfer_pts, c->w_iso, c->lr0, c->lr_growth, c->lambda0,
@@ -256,10 +282,14 @@ pdg_status upload_job(pdg_ctx* c, cudaStream_t s) {
 
 // The step as an explicit list of stages; the graph capture and the profiling path launch
 // exactly the same sequence.
-const char* const STAGE_NAMES[] = {"interp",     "mov_scan", "mov_scatter", "nn",          "nn_hard",
-                                   "iso_edges",  "assemble", "adjoint",     "sob_xy_fwd",  "sob_z",
-                                   "sob_xy_inv", "adam",     "sobolev_256", "loss"};
+const char* const STAGE_NAMES[] = {"interp",     "nn_fwd",     "mov_scan", "mov_scatter", "nn_rev",
+                                   "nn_hard",    "iso_edges",  "assemble", "adjoint",     "sob_xy_fwd",
+                                   "sob_z",      "sob_xy_inv", "adam",     "sobolev_256", "loss"};
 constexpr int N_STAGES = sizeof(STAGE_NAMES) / sizeof(STAGE_NAMES[0]);
+enum StageIndex {
+  S_INTERP = 0, S_NN_FWD, S_MOV_SCAN, S_MOV_SCATTER, S_NN_REV, S_NN_HARD, S_ISO, S_ASSEMBLE, S_ADJOINT,
+  S_SOB_XY_FWD, S_SOB_Z, S_SOB_XY_INV, S_ADAM, S_SOB_256, S_LOSS
+};
 
 // Stage i of a step; bump: the job_bump mode of the interpolation stage (1: optimisation
 // step, 2: evaluation).  The plan's item prefixes must be current (refresh_plan).
@@ -268,34 +298,36 @@ void launch_stage(int i, const Plan* plan, int nmax, int sms, cudaStream_t s, in
   const int smem = sobolev_smem_bytes(nmax);
   const int tiles_per_sm = std::max(1, std::min(4, (227 * 1024) / std::max(smem, 1)));
   switch (i) {
-    case 0: launch_interp(plan, grid, s, bump); break;
-    case 1: launch_mov_scan(plan, sms * 2, s); break;
-    case 2: launch_mov_scatter(plan, grid, s); break;
-    case 3: launch_nn(plan, grid * 2, s); break;
-    case 4: launch_nn_hard(plan, sms * 4, s); break;
-    case 5: launch_iso_edges(plan, grid, s); break;
-    case 6: launch_assemble(plan, grid, s); break;
-    case 7: launch_adjoint(plan, grid * 2, s); break;
-    case 8:
-    case 9:
-    case 10:
-    case 11: {
+    case S_INTERP: launch_interp(plan, grid, s, bump); break;
+    case S_NN_FWD: launch_nn(plan, grid * 2, s, 1); break;
+    case S_MOV_SCAN: launch_mov_scan(plan, sms * 2, s); break;
+    case S_MOV_SCATTER: launch_mov_scatter(plan, grid, s); break;
+    case S_NN_REV: launch_nn(plan, grid * 2, s, 2); break;
+    case S_NN_HARD: launch_nn_hard(plan, sms * 4, s); break;
+    case S_ISO: launch_iso_edges(plan, grid, s); break;
+    case S_ASSEMBLE: launch_assemble(plan, grid, s); break;
+    case S_ADJOINT: launch_adjoint(plan, grid * 2, s); break;
+    case S_SOB_XY_FWD:
+    case S_SOB_Z:
+    case S_SOB_XY_INV:
+    case S_ADAM: {
       const int ps = plane_smem_max(nmax);
       const int per_sm = std::max(1, std::min(8, (227 * 1024) / ps));
-      launch_sobolev_plane(plan, sms * per_sm, nmax, s, i - 8);
+      launch_sobolev_plane(plan, sms * per_sm, nmax, s, i - S_SOB_XY_FWD);
       break;
     }
-    case 12:
+    case S_SOB_256:
       if (nmax > 128) launch_sobolev_tiles(plan, sms * tiles_per_sm, nmax, s);
       break;
-    case 13: launch_loss(plan, sms * 2, s); break;
+    case S_LOSS: launch_loss(plan, sms * 2, s); break;
   }
 }
-constexpr int ST_SOB_FIRST = 8, ST_SOB_LAST = 12;  // preconditioner and Adam stages
+constexpr int ST_SOB_FIRST = S_SOB_XY_FWD, ST_SOB_LAST = S_SOB_256;  // preconditioner and Adam stages
 
-// Captures one step.  Two branches: the isometry kernel runs beside the nearest-neighbour
-// stages (it needs only the deformed points), the loss reduction beside the adjoint and
-// the preconditioner (nothing downstream reads it).
+// Captures one step.  Two branches: the forward nearest-neighbour pass (it needs the
+// per-frame target grid and the deformed points, not the moving grid) and the isometry
+// kernel run beside the moving grid's sort and the reverse pass; the loss reduction runs
+// beside the adjoint and the preconditioner (nothing downstream reads it).
 pdg_status capture_step(pdg_ctx* c, const Plan* plan, int nmax, cudaStream_t cap, cudaStream_t cap2,
                         cudaGraphExec_t* out, std::string* err, int sms, int* n_kernels = nullptr) {
   cudaGraph_t g = nullptr;
@@ -311,19 +343,23 @@ pdg_status capture_step(pdg_ctx* c, const Plan* plan, int nmax, cudaStream_t cap
     for (auto& x : ev) cudaEventDestroy(x);
     return PDG_ERR_CUDA;
   }
-  launch_stage(0, plan, nmax, sms, cap);  // interp (starts the step of every job)
+  launch_stage(S_INTERP, plan, nmax, sms, cap);  // starts the step of every job
   cudaEventRecord(ev[0], cap);
   cudaStreamWaitEvent(cap2, ev[0], 0);
-  launch_stage(5, plan, nmax, sms, cap2);  // iso_edges
+  launch_stage(S_NN_FWD, plan, nmax, sms, cap2);
+  launch_stage(S_ISO, plan, nmax, sms, cap2);
   cudaEventRecord(ev[1], cap2);
-  for (int i = 1; i <= 4; ++i) launch_stage(i, plan, nmax, sms, cap);  // moving grid, NN
+  launch_stage(S_MOV_SCAN, plan, nmax, sms, cap);
+  launch_stage(S_MOV_SCATTER, plan, nmax, sms, cap);
+  launch_stage(S_NN_REV, plan, nmax, sms, cap);
   cudaStreamWaitEvent(cap, ev[1], 0);
-  launch_stage(6, plan, nmax, sms, cap);  // assemble
+  launch_stage(S_NN_HARD, plan, nmax, sms, cap);
+  launch_stage(S_ASSEMBLE, plan, nmax, sms, cap);
   cudaEventRecord(ev[2], cap);
   cudaStreamWaitEvent(cap2, ev[2], 0);
-  launch_stage(13, plan, nmax, sms, cap2);  // loss
+  launch_stage(S_LOSS, plan, nmax, sms, cap2);
   cudaEventRecord(ev[3], cap2);
-  for (int i = 7; i <= 12; ++i) launch_stage(i, plan, nmax, sms, cap);  // adjoint, preconditioner, Adam
+  for (int i = S_ADJOINT; i <= S_SOB_256; ++i) launch_stage(i, plan, nmax, sms, cap);  // adjoint, preconditioner, Adam
   cudaStreamWaitEvent(cap, ev[3], 0);
   e = cudaStreamEndCapture(cap, &g);
   for (auto& x : ev) cudaEventDestroy(x);
@@ -384,6 +420,7 @@ void pdg_config_default(pdg_config* c) {
   c->precondition = 1;
   c->robust_weight_stopgrad = 0;
   c->warm_start = 0;
+  c->payload = PDG_PAYLOAD_DISPLACEMENT;
 }
 
 size_t pdg_query_bytes(const pdg_config* cfg, int n_verts, int n_edges, int max_pts) {
@@ -468,7 +505,7 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
   }
 
   const Layout L = make_layout(*cfg, n_verts, n_edges, max_pts);
-  if (cudaMalloc(&c->arena, L.total) != cudaSuccess) {
+  if (dev_malloc((void**)&c->arena, L.total) != cudaSuccess) {
     cudaGetLastError();
     c->arena = nullptr;
     return bail(PDG_ERR_OOM);
@@ -480,6 +517,7 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
   Job& J = c->h;
   std::memset(&J, 0, sizeof(J));
   J.L = cfg->n_levels;
+  J.C = cfg->payload == PDG_PAYLOAD_CAYLEY ? 6 : 3;
   for (int a = 0; a < 3; ++a) {
     J.lo[a] = cfg->lo[a];
     J.hi[a] = cfg->hi[a];
@@ -524,6 +562,7 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
       lv.sc_lo[a] = (float)(sc - (double)lv.sc_hi[a]);
     }
     lv.theta = (float4*)P(o.theta);
+    lv.theta_t = J.C == 6 ? (float4*)P(o.theta_t) : nullptr;
     lv.m = (float*)P(o.m);
     lv.v = (float*)P(o.v);
     lv.g = (float*)P(o.g);
@@ -534,12 +573,12 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
     lv.mu = (float*)P(o.mu);
     lv.tw = (float2*)P(o.tw);
     lv.tw4 = (float2*)P(o.tw4);
-    lv.cnt = (int*)P(o.cnt);
-    lv.rowptr = (int*)P(o.rowptr);
+    lv.ccnt = (int*)P(o.ccnt);
+    lv.coff = (int*)P(o.coff);
+    lv.ckey = (int*)P(o.ckey);
+    lv.xs = (float4*)P(o.xs);
     lv.flag = (int*)P(o.flag);
     lv.act_v = (int*)P(o.act_v);
-    lv.act_ptr = (int*)P(o.act_ptr);
-    lv.ent = (int2*)P(o.ent);
     lv.n_active = (int*)P(o.n_active);
     lv.csum = (int*)P(o.csum);
     c->nmax = std::max(c->nmax, n);
@@ -564,6 +603,9 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
   J.y = (float4*)P(L.y);
   J.gfwd = (float4*)P(L.gfwd);
   J.gy = (float4*)P(L.gy);
+  J.zq = J.C == 6 ? (float4*)P(L.zq) : nullptr;
+  J.uq = J.C == 6 ? (float4*)P(L.uq) : nullptr;
+  J.gz = J.C == 6 ? (float4*)P(L.gz) : nullptr;
   J.acc = (long long*)P(L.acc);
   J.loss_fwd = (float*)P(L.loss_fwd);
   J.loss_rev = (float*)P(L.loss_rev);
@@ -603,6 +645,7 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
   J.loss = (double*)P(L.loss);
   J.status = (int*)P(L.status);
   J.gmax = (unsigned*)P(L.gmax);
+  J.counters = (unsigned long long*)P(L.counters);
 
   if (n_edges) {
     if (cudaMemcpyAsync((void*)J.edges, he.data(), he.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -637,9 +680,10 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
   return PDG_OK;
 }
 
-pdg_status pdg_set_debug(pdg_ctx* c, int keep_pgrad) {
-  if (!c) return PDG_ERR_INVALID;
-  c->h.keep_pgrad = keep_pgrad ? 1 : 0;
+pdg_status pdg_set_debug(pdg_ctx* c, int flags) {
+  if (!c || (flags & ~(PDG_DEBUG_KEEP_PGRAD | PDG_DEBUG_COUNT_NN))) return PDG_ERR_INVALID;
+  c->h.keep_pgrad = (flags & PDG_DEBUG_KEEP_PGRAD) ? 1 : 0;
+  c->h.count_nn = (flags & PDG_DEBUG_COUNT_NN) ? 1 : 0;
   return upload_job(c, 0) == PDG_OK ? c->cuda(cudaDeviceSynchronize(), "set_debug") : PDG_ERR_CUDA;
 }
 
@@ -666,10 +710,13 @@ pdg_status pdg_begin_frame(pdg_ctx* c, const float* target_xyz, int n_tgt, void*
   launch_frame_points(c->dJ, J.Q, J.E, s);
   for (int l = 0; l < J.L; ++l) {
     const Level& lv = J.lev[l];
-    if (!c->cfg.warm_start) CU(c, cudaMemsetAsync(lv.theta, 0, sizeof(float4) * lv.n3, s));
-    CU(c, cudaMemsetAsync(lv.m, 0, sizeof(float) * 3 * lv.n3, s));
-    CU(c, cudaMemsetAsync(lv.v, 0, sizeof(float) * 3 * lv.n3, s));
-    CU(c, cudaMemsetAsync(lv.g, 0, sizeof(float) * 3 * lv.n3, s));
+    if (!c->cfg.warm_start) {
+      CU(c, cudaMemsetAsync(lv.theta, 0, sizeof(float4) * lv.n3, s));
+      if (lv.theta_t) CU(c, cudaMemsetAsync(lv.theta_t, 0, sizeof(float4) * lv.n3, s));
+    }
+    CU(c, cudaMemsetAsync(lv.m, 0, sizeof(float) * J.C * lv.n3, s));
+    CU(c, cudaMemsetAsync(lv.v, 0, sizeof(float) * J.C * lv.n3, s));
+    CU(c, cudaMemsetAsync(lv.g, 0, sizeof(float) * J.C * lv.n3, s));
   }
   CU(c, cudaMemsetAsync(J.step, 0, sizeof(int), s));
   CU(c, cudaMemsetAsync(J.status, 0, sizeof(int), s));
@@ -748,8 +795,10 @@ pdg_status pdg_end_frame(pdg_ctx* c, pdg_fit_stats* stats, void* cuda_stream) {
   CU(c, cudaMemcpyAsync(J.src4, J.tgt4, sizeof(float4) * J.M, cudaMemcpyDeviceToDevice, s));
   double loss[4];
   int status = 0;
+  unsigned long long cnt[4] = {0, 0, 0, 0};
   CU(c, cudaMemcpyAsync(loss, J.loss, sizeof(loss), cudaMemcpyDeviceToHost, s));
   CU(c, cudaMemcpyAsync(&status, J.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CU(c, cudaMemcpyAsync(cnt, J.counters, sizeof(cnt), cudaMemcpyDeviceToHost, s));
   CU(c, cudaStreamSynchronize(s));
   J.N = J.M;
   J.Q = J.V + J.N;
@@ -762,6 +811,7 @@ pdg_status pdg_end_frame(pdg_ctx* c, pdg_fit_stats* stats, void* cuda_stream) {
     stats->iso = loss[3];
     stats->n_steps = c->steps_in_frame;
     stats->status = st;
+    stats->nn_ties = c->steps_in_frame > 0 ? (int)std::min<unsigned long long>(cnt[CNT_NN_TIES], 0x7fffffff) : 0;
   }
   if (st != PDG_OK) c->err = "a loss became NaN or Inf during the frame";
   return st;
@@ -784,16 +834,29 @@ pdg_status pdg_deform(pdg_ctx* c, const float* xyz, int n, float* out, void* cud
   if (n == 0) return PDG_OK;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const bool din = is_device_ptr(xyz), dout = is_device_ptr(out);
-  float* tmp = nullptr;
-  const size_t bytes = sizeof(float) * 3 * (size_t)n;
-  if (!din || !dout) CU(c, cudaMallocAsync((void**)&tmp, 2 * bytes, s));
-  const float* in = din ? xyz : tmp;
-  float* o = dout ? out : tmp + 3 * (size_t)n;
-  if (!din) CU(c, cudaMemcpyAsync(tmp, xyz, bytes, cudaMemcpyHostToDevice, s));
-  launch_deform(c->dJ, in, o, n, s);
-  if (!dout) CU(c, cudaMemcpyAsync(out, o, bytes, cudaMemcpyDeviceToHost, s));
-  if (tmp) CU(c, cudaFreeAsync(tmp, s));
-  if (!din || !dout) CU(c, cudaStreamSynchronize(s));
+  if (din && dout) {
+    launch_deform(c->dJ, xyz, out, n, s);
+    return c->cuda(cudaGetLastError(), "deform");
+  }
+  // host buffers go through the context's staging area in chunks (no allocation): the first
+  // half of the area holds the chunk's input, the second its output
+  const int chunk = std::max(1, c->stage_pts / 2);
+  float* sin_ = c->stage;
+  float* sout = c->stage + 3 * (size_t)chunk;
+  for (int b = 0; b < n; b += chunk) {
+    const int m = std::min(chunk, n - b);
+    const size_t bytes = sizeof(float) * 3 * (size_t)m;
+    const float* in = xyz + 3 * (size_t)b;
+    float* o = out + 3 * (size_t)b;
+    if (!din) {
+      CU(c, cudaMemcpyAsync(sin_, in, bytes, cudaMemcpyHostToDevice, s));
+      in = sin_;
+    }
+    launch_deform(c->dJ, in, dout ? o : sout, m, s);
+    if (!dout) CU(c, cudaMemcpyAsync(o, sout, bytes, cudaMemcpyDeviceToHost, s));
+    // the next chunk overwrites the staging area: wait until this one has left it
+    CU(c, cudaStreamSynchronize(s));
+  }
   return c->cuda(cudaGetLastError(), "deform");
 }
 
@@ -812,12 +875,13 @@ pdg_status pdg_get_vertices(pdg_ctx* c, float* out, void* cuda_stream) {
   if (!c || !out) return PDG_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const size_t bytes = sizeof(float) * 3 * (size_t)c->V;
-  float* tmp = nullptr;
-  CU(c, cudaMallocAsync((void**)&tmp, bytes, s));
-  launch_unpack4(c->h.verts4, tmp, c->V, s);
-  const pdg_status st = copy_out(c, out, tmp, bytes, s);
-  cudaFreeAsync(tmp, s);
-  return st;
+  if (is_device_ptr(out)) {
+    launch_unpack4(c->h.verts4, out, c->V, s);
+    return c->cuda(cudaGetLastError(), "get_vertices");
+  }
+  // through the staging area (it holds max(V, max_pts) points): no allocation
+  launch_unpack4(c->h.verts4, c->stage, c->V, s);
+  return copy_out(c, out, c->stage, bytes, s);
 }
 
 pdg_status pdg_read(pdg_ctx* c, int which, int level, void* out, size_t out_bytes, void* cuda_stream) {
@@ -830,13 +894,14 @@ pdg_status pdg_read(pdg_ctx* c, int which, int level, void* out, size_t out_byte
   switch (which) {
     case PDG_BUF_THETA:
     case PDG_BUF_GRAD:
-    case PDG_BUF_PGRAD: need = sizeof(float) * 3 * (size_t)J.lev[level].n3; break;
+    case PDG_BUF_PGRAD: need = sizeof(float) * J.C * (size_t)J.lev[level].n3; break;
     case PDG_BUF_Y:
     case PDG_BUF_POINT_GRAD: need = sizeof(float) * 3 * (size_t)J.Q; break;
     case PDG_BUF_NN_FWD: need = sizeof(int) * (size_t)J.Q; break;
     case PDG_BUF_NN_REV: need = sizeof(int) * 2 * (size_t)J.M; break;
     case PDG_BUF_LOSS: need = 4 * sizeof(double); break;
     case PDG_BUF_SOURCE: need = sizeof(float) * 3 * (size_t)J.N; break;
+    case PDG_BUF_COUNTERS: need = 4 * sizeof(unsigned long long); break;
     default: return c->fail(PDG_ERR_INVALID, "unknown buffer");
   }
   if (out_bytes < need) return c->fail(PDG_ERR_INVALID, "output buffer too small");
@@ -844,13 +909,16 @@ pdg_status pdg_read(pdg_ctx* c, int which, int level, void* out, size_t out_byte
   if (which == PDG_BUF_LOSS) return copy_out(c, out, J.loss, need, s);
   if (which == PDG_BUF_NN_FWD) return copy_out(c, out, J.nn_fwd, need, s);
   if (which == PDG_BUF_NN_REV) return copy_out(c, out, J.nn_rev, need, s);
+  if (which == PDG_BUF_COUNTERS) return copy_out(c, out, J.counters, need, s);
   float* tmp = nullptr;
   CU(c, cudaMallocAsync((void**)&tmp, need, s));
   switch (which) {
-    case PDG_BUF_THETA: launch_unpack4(J.lev[level].theta, tmp, J.lev[level].n3, s); break;
-    case PDG_BUF_GRAD: launch_soa_to_aos(J.lev[level].g, tmp, J.lev[level].n3, s); break;
+    case PDG_BUF_THETA:
+      launch_unpack_theta(J.lev[level].theta, J.lev[level].theta_t, tmp, J.lev[level].n3, J.C, s);
+      break;
+    case PDG_BUF_GRAD: launch_soa_to_aos(J.lev[level].g, tmp, J.lev[level].n3, s, J.C); break;
     case PDG_BUF_PGRAD:  // without the preconditioner Adam takes the raw gradient
-      launch_soa_to_aos(J.precondition ? J.lev[level].tmp : J.lev[level].g, tmp, J.lev[level].n3, s);
+      launch_soa_to_aos(J.precondition ? J.lev[level].tmp : J.lev[level].g, tmp, J.lev[level].n3, s, J.C);
       break;
     case PDG_BUF_Y: launch_unpack4(J.y, tmp, J.Q, s); break;
     case PDG_BUF_POINT_GRAD: launch_unpack4(J.gy, tmp, J.Q, s); break;
@@ -868,15 +936,16 @@ pdg_status pdg_write_theta(pdg_ctx* c, int level, const float* theta, void* cuda
   const Level& lv = c->h.lev[level];
   const float* src = theta;
   float* tmp = nullptr;
-  const size_t bytes = sizeof(float) * 3 * (size_t)lv.n3;
+  const int C = c->h.C;
+  const size_t bytes = sizeof(float) * C * (size_t)lv.n3;
   if (!is_device_ptr(theta)) {
     CU(c, cudaMallocAsync((void**)&tmp, bytes, s));
     CU(c, cudaMemcpyAsync(tmp, theta, bytes, cudaMemcpyHostToDevice, s));
     src = tmp;
   }
-  launch_pack4(src, lv.theta, lv.n3, s);
-  CU(c, cudaMemsetAsync(lv.m, 0, 3 * sizeof(float) * lv.n3, s));
-  CU(c, cudaMemsetAsync(lv.v, 0, 3 * sizeof(float) * lv.n3, s));
+  launch_pack_theta(src, lv.theta, lv.theta_t, lv.n3, C, s);
+  CU(c, cudaMemsetAsync(lv.m, 0, C * sizeof(float) * lv.n3, s));
+  CU(c, cudaMemsetAsync(lv.v, 0, C * sizeof(float) * lv.n3, s));
   if (tmp) {
     CU(c, cudaFreeAsync(tmp, s));
     CU(c, cudaStreamSynchronize(s));
@@ -913,6 +982,7 @@ pdg_status pdg_precondition(pdg_ctx* c, int level, const float* g, float* out, v
   // a one-level copy of the job that stores the preconditioned gradient instead of Adam
   Job oj = c->h;
   oj.L = 1;
+  oj.C = 3;  // the entry point preconditions 3 channels whatever the payload
   oj.lev[0] = lv;
   oj.lev[0].zmask = nullptr;  // a caller's gradient may be non-zero on any plane
   oj.precondition = 1;
@@ -937,11 +1007,13 @@ pdg_status pdg_precondition(pdg_ctx* c, int level, const float* g, float* out, v
 
 // ------------------------------------------------------------------------------ batching
 
+void pdg_debug_fail_allocations(int n) { g_fail_allocs.store(n > 0 ? n : 0); }
+
 pdg_status pdg_batch_create(int max_jobs, pdg_batch** out) {
   if (!out || max_jobs < 1 || max_jobs > MAXJ) return PDG_ERR_INVALID;
   pdg_batch* b = new pdg_batch();
   b->max_jobs = max_jobs;
-  if (cudaMalloc(&b->dplan, sizeof(Plan)) != cudaSuccess || cudaMallocHost(&b->hplan, sizeof(Plan)) != cudaSuccess ||
+  if (dev_malloc((void**)&b->dplan, sizeof(Plan)) != cudaSuccess || cudaMallocHost(&b->hplan, sizeof(Plan)) != cudaSuccess ||
       cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&b->cap2, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
@@ -1033,14 +1105,14 @@ pdg_status pdg_batch_step(pdg_batch* b, int n_steps, void* cuda_stream) {
 namespace {
 struct StateHeader {
   char magic[8];
-  int version, V, N, L, res[PDG_MAX_LEVELS];
+  int version, V, N, L, res[PDG_MAX_LEVELS], C;
 };
 }  // namespace
 
 size_t pdg_state_bytes(const pdg_ctx* c) {
   if (!c) return 0;
   size_t b = sizeof(StateHeader) + sizeof(float4) * (size_t)c->V + sizeof(float4) * (size_t)c->max_pts;
-  for (int l = 0; l < c->h.L; ++l) b += sizeof(float4) * (size_t)c->h.lev[l].n3;
+  for (int l = 0; l < c->h.L; ++l) b += sizeof(float4) * (size_t)c->h.lev[l].n3 * (c->h.C / 3);
   return b;
 }
 
@@ -1051,8 +1123,9 @@ pdg_status pdg_save_state(pdg_ctx* c, void* host_buf, size_t n, void* cuda_strea
   cudaStream_t s = (cudaStream_t)cuda_stream;
   StateHeader hd{};
   std::memcpy(hd.magic, "PDGSTAT", 8);
-  hd.version = 1;
+  hd.version = 2;
   hd.V = c->V;
+  hd.C = c->h.C;
   hd.N = c->h.N;
   hd.L = c->h.L;
   for (int l = 0; l < c->h.L; ++l) hd.res[l] = c->h.lev[l].n;
@@ -1066,6 +1139,10 @@ pdg_status pdg_save_state(pdg_ctx* c, void* host_buf, size_t n, void* cuda_strea
   for (int l = 0; l < c->h.L; ++l) {
     CU(c, cudaMemcpyAsync(p, c->h.lev[l].theta, sizeof(float4) * c->h.lev[l].n3, cudaMemcpyDeviceToHost, s));
     p += sizeof(float4) * c->h.lev[l].n3;
+    if (c->h.C == 6) {
+      CU(c, cudaMemcpyAsync(p, c->h.lev[l].theta_t, sizeof(float4) * c->h.lev[l].n3, cudaMemcpyDeviceToHost, s));
+      p += sizeof(float4) * c->h.lev[l].n3;
+    }
   }
   CU(c, cudaStreamSynchronize(s));
   return PDG_OK;
@@ -1077,7 +1154,7 @@ pdg_status pdg_load_state(pdg_ctx* c, const void* host_buf, size_t n, void* cuda
   if (n < pdg_state_bytes(c)) return c->fail(PDG_ERR_INVALID, "state buffer too small");
   StateHeader hd;
   std::memcpy(&hd, host_buf, sizeof(hd));
-  if (std::memcmp(hd.magic, "PDGSTAT", 8) != 0 || hd.version != 1 || hd.V != c->V || hd.L != c->h.L ||
+  if (std::memcmp(hd.magic, "PDGSTAT", 8) != 0 || hd.version != 2 || hd.V != c->V || hd.L != c->h.L || hd.C != c->h.C ||
       hd.N < 1 || hd.N > c->max_pts)
     return c->fail(PDG_ERR_INVALID, "state does not match this context");
   for (int l = 0; l < c->h.L; ++l)
@@ -1091,6 +1168,10 @@ pdg_status pdg_load_state(pdg_ctx* c, const void* host_buf, size_t n, void* cuda
   for (int l = 0; l < c->h.L; ++l) {
     CU(c, cudaMemcpyAsync(c->h.lev[l].theta, p, sizeof(float4) * c->h.lev[l].n3, cudaMemcpyHostToDevice, s));
     p += sizeof(float4) * c->h.lev[l].n3;
+    if (c->h.C == 6) {
+      CU(c, cudaMemcpyAsync(c->h.lev[l].theta_t, p, sizeof(float4) * c->h.lev[l].n3, cudaMemcpyHostToDevice, s));
+      p += sizeof(float4) * c->h.lev[l].n3;
+    }
   }
   c->h.N = hd.N;
   c->h.Q = c->V + hd.N;

@@ -7,10 +7,10 @@ frames of different sequences overlap on the device:
 * every sequence owns one resident context (template, current source cloud, grids and
   optimiser state stay on the device across frames), created on its first request if the
   device-memory budget allows (`pdg_query_bytes`), otherwise the request waits;
-* at every iteration boundary the server admits waiting frames whose sequence is idle
-  (`pdg_begin_frame`), retires finished frames (`pdg_end_frame`), and runs one
-  optimisation iteration of every live frame as a single CUDA-graph launch of batched
-  kernels (`pdg_batch_step`);
+* at every boundary of at most `chunk` iterations the server admits waiting frames whose
+  sequence is idle (`pdg_begin_frame`, on a side stream, from host memory), retires finished
+  frames (`pdg_end_frame`), and runs the next iterations of every live frame, each one CUDA-
+  graph launch of batched kernels (`pdg_batch_step`);
 * the batch has `max_slots` slots; a sequence's context is released when its last frame
   is done, freeing budget for new sequences.
 
@@ -74,7 +74,15 @@ def _percentiles(lat):
 
 
 class Server:
-    def __init__(self, seqs, steps: int, budget_bytes: int, max_slots: int = 64, device=None, cfg_kwargs=None):
+    """Continuous batching of per-frame fitting requests on one GPU.
+
+    `chunk` bounds the iterations one batch launch runs, so a frame that arrives while
+    others are on the GPU joins them at the next boundary of at most `chunk` iterations
+    (its set-up runs on a side stream meanwhile, from host memory); the host stays at most one
+    chunk ahead of the GPU."""
+
+    def __init__(self, seqs, steps: int, budget_bytes: int, max_slots: int = 64, device=None, cfg_kwargs=None,
+                 chunk: int = 4):
         import torch
 
         from . import binding as B
@@ -86,24 +94,27 @@ class Server:
         self.steps = steps
         self.budget = budget_bytes
         self.max_slots = max_slots
+        self.chunk = max(1, int(chunk))
         self.cfg_kwargs = cfg_kwargs or {}
         self.used = 0
         self.ctx = {}  # sid -> context handle
         self.bytes = {}
         self.batch = B.pdg_batch_create(max_slots)
+        # two non-blocking streams (neither waits for the legacy default stream): batched
+        # iterations on `main`, frame set-up on `admit`
+        self.main = torch.cuda.Stream(self.dev)
+        self.admit = torch.cuda.Stream(self.dev)
 
     def _cfg(self, s):
         return self.B.pdg_config_default(res=s.res, **self.cfg_kwargs)
-
-    def _dev(self, a):
-        return self.torch.from_numpy(np.ascontiguousarray(a)).to(self.dev)
 
     def _open(self, s):
         need = self.B.pdg_query_bytes(self._cfg(s), len(s.template), len(s.edges), s.max_pts)
         if self.used + need > self.budget:
             return False
-        self.ctx[s.sid] = self.B.pdg_create(self._cfg(s), self._dev(s.template), self._dev(s.edges),
-                                            self._dev(s.source0), max_pts=s.max_pts)
+        # host arrays: the library copies them on the side stream
+        self.ctx[s.sid] = self.B.pdg_create(self._cfg(s), s.template, s.edges, s.source0, max_pts=s.max_pts,
+                                            stream=self.admit.cuda_stream)
         self.bytes[s.sid] = need
         self.used += need
         return True
@@ -115,20 +126,24 @@ class Server:
     def run(self, trace, realtime: bool = True):
         """Serves the trace; returns per-request records and summary statistics."""
         B = self.B
+        main = self.main.cuda_stream
         waiting = collections.deque(sorted(trace, key=lambda r: r.arrival))
         arrived: list[Request] = []
-        live = {}  # sid -> (request, steps done)
+        live = {}  # sid -> [request, steps done]
         busy = set()
-        done = []
         remaining = {sid: len(s.frames) for sid, s in self.seqs.items()}
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0
         members_changed = True
+        prev_ev = None
         while waiting or arrived or live:
             t = now()
             while waiting and (waiting[0].arrival <= t or not realtime):
                 arrived.append(waiting.popleft())
-            # admit frames in arrival order: sequence idle, slot free, context resident
+            # admit frames in arrival order: sequence idle, slot free, context resident; their
+            # set-up runs on the side stream (host target copied by the library), beside the
+            # batch's iterations on the main stream
+            admitted = False
             for r in list(arrived):
                 if len(live) >= self.max_slots:
                     break
@@ -137,12 +152,15 @@ class Server:
                 s = self.seqs[r.sid]
                 if r.sid not in self.ctx and not self._open(s):
                     continue
-                B.pdg_begin_frame(self.ctx[r.sid], self._dev(s.frames[r.frame]))
+                B.pdg_begin_frame(self.ctx[r.sid], s.frames[r.frame], stream=self.admit.cuda_stream)
                 r.admitted = now()
                 live[r.sid] = [r, 0]
                 busy.add(r.sid)
                 arrived.remove(r)
                 members_changed = True
+                admitted = True
+            if admitted:
+                self.main.wait_stream(self.admit)  # new members' set-up precedes their first step
             if not live:
                 if waiting and realtime:
                     time.sleep(max(0.0, min(waiting[0].arrival - now(), 0.001)))
@@ -150,25 +168,31 @@ class Server:
             if members_changed:
                 B.pdg_batch_set(self.batch, [self.ctx[sid] for sid in live])
                 members_changed = False
-            # iterations until the next frame finishes (no membership change before then)
-            k = min(self.steps - st for _, st in live.values())
-            B.pdg_batch_step(self.batch, k)
+            # at most `chunk` iterations, fewer if a frame finishes sooner
+            k = min(self.chunk, min(self.steps - st for _, st in live.values()))
+            B.pdg_batch_step(self.batch, k, stream=main)
+            ev = self.torch.cuda.Event()
+            ev.record(self.main)
+            finished = False
             for sid in list(live):
                 live[sid][1] += k
                 r, st = live[sid]
                 if st >= self.steps:
-                    stats = B.pdg_end_frame(self.ctx[sid])
+                    stats = B.pdg_end_frame(self.ctx[sid], stream=main)  # synchronises the main stream
                     r.finished = now()
                     r.loss = stats.loss_total
                     del live[sid]
                     busy.discard(sid)
                     remaining[sid] -= 1
                     members_changed = True
+                    finished = True
                     if remaining[sid] == 0:
                         r.vertices = B.pdg_get_vertices(self.ctx[sid], np.empty((len(self.seqs[sid].template), 3),
-                                                                                np.float32))
+                                                                                np.float32), stream=main)
                         self._close(sid)
-            # new arrivals may be admitted at the next boundary
+            if not finished and prev_ev is not None:
+                prev_ev.synchronize()  # at most one chunk queued ahead of the GPU
+            prev_ev = ev
         wall = now()
         lat = [r.finished - r.arrival for r in trace]
         p50, p99 = _percentiles(lat)
@@ -190,23 +214,23 @@ def serve_plain(seqs, trace, steps: int, device=None, cfg_kwargs=None, realtime:
     byid = {s.sid: s for s in seqs}
     ctx = {}
     remaining = {s.sid: len(s.frames) for s in seqs}
-    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
     t0 = time.perf_counter()
     now = lambda: time.perf_counter() - t0
     for r in sorted(trace, key=lambda r: r.arrival):
         if realtime and r.arrival > now():
             time.sleep(r.arrival - now())
         s = byid[r.sid]
-        if r.sid not in ctx:
-            ctx[r.sid] = B.pdg_create(B.pdg_config_default(res=s.res, **(cfg_kwargs or {})), T(s.template),
-                                      T(s.edges), T(s.source0), max_pts=s.max_pts)
+        if r.sid not in ctx:  # host arrays: the library copies them
+            ctx[r.sid] = B.pdg_create(B.pdg_config_default(res=s.res, **(cfg_kwargs or {})), s.template,
+                                      s.edges, s.source0, max_pts=s.max_pts, stream=stream)
         r.admitted = now()
-        st = B.pdg_fit_frame(ctx[r.sid], T(s.frames[r.frame]), steps)
+        st = B.pdg_fit_frame(ctx[r.sid], s.frames[r.frame], steps, stream=stream)
         r.finished = now()
         r.loss = st.loss_total
         remaining[r.sid] -= 1
         if remaining[r.sid] == 0:
-            r.vertices = B.pdg_get_vertices(ctx[r.sid], np.empty((len(s.template), 3), np.float32))
+            r.vertices = B.pdg_get_vertices(ctx[r.sid], np.empty((len(s.template), 3), np.float32), stream=stream)
             B.pdg_destroy(ctx.pop(r.sid))
     wall = now()
     lat = [r.finished - r.arrival for r in trace]

@@ -278,15 +278,16 @@ def smooth_pow2(n: float) -> int:
     return int(2 ** round(math.log2(max(n, 2))))
 
 
-def batched_job(i: int, scale: float = 1.0):
+def batched_job(i: int, scale: float = 1.0, n_pts: int | None = None):
     """Job i of the batched / served workload: shape in {sphere, torus, ellipsoid},
-    points per frame log-uniform in [5k, 200k] (times `scale`), 3-5 levels with the finest
+    points per frame log-uniform in [5k, 200k] (times `scale`; `n_pts` overrides the draw,
+    e.g. for the 500k-point frames of the served trace), 3-5 levels with the finest
     log-uniform in [32, 256] vertices per axis (rounded to a power of two), and an
     analytic deformation in {twist, bend, sinusoid}.  Returns a dict of arrays/params."""
     rng = np.random.Generator(np.random.PCG64(1000 + i))
     shape = ["sphere", "torus", "ellipsoid"][rng.integers(3)]
-    n_pts = int(math.exp(rng.uniform(math.log(5e3), math.log(2e5))) * scale)
-    n_pts = max(n_pts, 256)
+    drawn = int(math.exp(rng.uniform(math.log(5e3), math.log(2e5))) * scale)
+    n_pts = max(drawn if n_pts is None else int(n_pts), 256)
     L = int(rng.integers(3, 6))
     finest = smooth_pow2(math.exp(rng.uniform(math.log(32), math.log(256))))
     res = tuple(max(4, smooth_pow2(finest / 2 ** (L - 1 - l))) for l in range(L))
