@@ -110,7 +110,7 @@ class ClockSampler:
 # kernel of each profiled stage and the source file that defines it
 STAGE_KERNEL = {
     "interp": ("k_interp", "k_points.cu"), "mov_scatter": ("k_mov_scatter", "k_points.cu"),
-    "nn_fwd": ("k_nn", "k_nn.cu"), "nn_rev": ("k_nn", "k_nn.cu"), "nn_hard": ("k_nn_hard", "k_nn.cu"), "adjoint": ("k_adjoint", "k_adjoint.cu"),
+    "nn": ("k_nn", "k_nn.cu"), "nn_hard": ("k_nn_hard", "k_nn.cu"), "adjoint": ("k_adjoint", "k_adjoint.cu"),
     "sob_xy_fwd": ("k_sobp", "k_sobolev_plane.cu"), "sob_z": ("k_sobz", "k_sobolev_plane.cu"),
     "sob_xy_inv": ("k_sobp_inv", "k_sobolev_plane.cu"), "adam": ("k_adam", "k_sobolev_plane.cu"),
     "iso_edges": ("k_iso_edges", "k_points.cu"),
@@ -191,7 +191,7 @@ def stage_model(stage, Q, V, M, E, res, act):
         return "hbm", Q * 24 + A * 12, "B"
     if stage == "adjoint":  # read dL/dy (16 B per point), write each touched grid gradient
         return "hbm", Q * 16 + A * 12, "B"
-    if stage in ("nn_fwd", "nn_rev", "nn_hard"):
+    if stage in ("nn", "nn_hard"):
         return "alu", None, "FLOP"
     if stage == "iso_edges":
         return "hbm", E * (8 + 4 + 4 + 12) + V * 12, "B"
@@ -232,10 +232,11 @@ def run_serving(n_seq=32, n_frames=2, steps=100, rate_hz=100.0, scale=1.0, budge
 
     seqs = serving_sequences(n_seq, n_frames, scale=scale)
     out = {"sequences": n_seq, "frames": n_seq * n_frames, "steps_per_frame": steps, "rate_hz": rate_hz,
+           "slots": SERVE_SLOTS,
            "points_per_frame": [int(min(len(f) for s_ in seqs for f in s_.frames)),
                                 int(max(len(f) for s_ in seqs for f in s_.frames))],
            "finest_res": [int(min(s_.res[-1] for s_ in seqs)), int(max(s_.res[-1] for s_ in seqs))]}
-    srv = serve.Server(seqs, steps=steps, budget_bytes=int(budget_gb * 1e9), max_slots=64)
+    srv = serve.Server(seqs, steps=steps, budget_bytes=int(budget_gb * 1e9), max_slots=SERVE_SLOTS)
     b = srv.run(serve.poisson_trace(seqs, rate_hz, seed=1), realtime=True)
     srv.close()
     p = serve.serve_plain(seqs, serve.poisson_trace(seqs, rate_hz, seed=1), steps, realtime=True)
@@ -243,6 +244,13 @@ def run_serving(n_seq=32, n_frames=2, steps=100, rate_hz=100.0, scale=1.0, budge
         out[k] = {"frames_per_s": r["frames_per_s"], "p50_ms": 1e3 * r["p50_s"], "p99_ms": 1e3 * r["p99_s"],
                   "wall_s": r["wall_s"]}
     return out
+
+
+# Live frames of the served runs: enough jobs per batched launch to amortise launches and
+# fill the GPU with small jobs, few enough that frames finish near arrival order (with every
+# queued frame admitted at once, an overloaded server shares the GPU between all of them and
+# every frame finishes late).
+SERVE_SLOTS = 8
 
 
 def serving_sequences(n_seq, n_frames, scale=1.0, big_every=0, big_pts=500_000):
@@ -279,13 +287,13 @@ def run_serving_scale(steps=100, budget_gb=150.0):
                             "plain": {k: p[k] for k in ("frames_per_s", "wall_s")}}
     seqs = serving_sequences(256, 2, big_every=20)
     out["served_256"] = {"sequences": 256, "frames_per_sequence": 2, "big_500k_sequences": 256 // 20,
-                         "budget_gb": budget_gb, "rates": {}}
+                         "budget_gb": budget_gb, "slots": SERVE_SLOTS, "rates": {}}
     for rate in (50.0, 100.0, 200.0, 400.0):
         r = {}
         for mode in ("batched", "plain"):
             tr = serve.poisson_trace(seqs, rate, seed=7)
             if mode == "batched":
-                srv = serve.Server(seqs, steps=steps, budget_bytes=int(budget_gb * 1e9), max_slots=256)
+                srv = serve.Server(seqs, steps=steps, budget_bytes=int(budget_gb * 1e9), max_slots=SERVE_SLOTS)
                 st = srv.run(tr, realtime=True)
                 srv.close()
             else:
@@ -496,7 +504,7 @@ def main():
     sm_mhz = clocks["sm_mhz"] or sm_max
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
-    nn_ms = prof["nn_fwd"] + prof["nn_rev"] + prof["nn_hard"]
+    nn_ms = prof["nn"] + prof["nn_hard"]
     stages = {}
     for k, ms in prof.items():
         b_, a_, u_ = stage_model(k, Q, V, M, E, w.res, act)
@@ -514,16 +522,15 @@ def main():
                            "TFLOP/s": round(8 * nn_cands / (nn_ms / 1e3) / 1e12, 3),
                            "frac_fp32": round(8 * nn_cands / (nn_ms / 1e3) / 1e12 / fp32_peak, 4)}
     grouped = dict(prof)
-    grouped["nn"] = nn_ms  # the search's three passes form one stage of the step
-    for k in ("nn_fwd", "nn_rev", "nn_hard"):
-        grouped.pop(k)
+    grouped["nn"] = nn_ms  # the search's two passes form one stage of the step
+    grouped.pop("nn_hard")
     dom = max(grouped, key=grouped.get)
-    bound, amount, unit = stage_model("nn_fwd" if dom == "nn" else dom, Q, V, M, E, w.res, act)
+    bound, amount, unit = stage_model(dom, Q, V, M, E, w.res, act)
     if bound == "alu":
         amount = 8.0 * nn_cands
         achieved = amount / (nn_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                "traffic": measured_traffic("nn_fwd"), "kernel": "k_nn (forward + reverse) + k_nn_hard",
+                "traffic": measured_traffic("nn"), "kernel": "k_nn + k_nn_hard",
                 "algorithmic_flops": amount,
                 "peak_note": f"FP32 {sms} SMs x 128 FMA x 2 at {sm_mhz:.0f} MHz (measured clock); 8 FLOP per squared "
                              f"distance the search evaluated ({nn_cands:.4g} per step, counted by the kernels)"}

@@ -93,7 +93,8 @@ typedef struct pdg_fit_stats {
   int status;        /* pdg_status of the frame */
   int nn_ties;       /* nearest-neighbour queries of the last iteration whose neighbour was decided
                         by an exact tie of fp32 squared distances (the lowest index won; a reading,
-                        the paper does not say how ties break) */
+                        the paper does not say how ties break); counted only while
+                        PDG_DEBUG_COUNT_NN is set, else -1 */
 } pdg_fit_stats;
 
 typedef struct pdg_ctx pdg_ctx;
@@ -154,9 +155,9 @@ enum pdg_buffer {
   PDG_BUF_LOSS = 7,     /* double [4]: total, cd_mesh, cd_pts, iso of the last step */
   PDG_BUF_SOURCE = 8,   /* current source cloud P_{t-1}, float [n_src][3] */
   PDG_BUF_COUNTERS = 9  /* uint64 [4] of the last step: squared distances the nearest-neighbour
-                           search evaluated (counted only with PDG_DEBUG_COUNT_NN, else 0),
-                           queries decided by an exact tie, queries left to the warp-cooperative
-                           ring search, 0 */
+                           search evaluated and queries decided by an exact tie (both counted
+                           only with PDG_DEBUG_COUNT_NN, else 0), queries left to the
+                           warp-cooperative ring search, 0 */
 };
 pdg_status pdg_read(pdg_ctx* ctx, int which, int level, void* out, size_t out_bytes, void* cuda_stream);
 
@@ -193,11 +194,13 @@ pdg_status pdg_eval(pdg_ctx* ctx, double* loss, void* cuda_stream);
  * gradient buffers are used as scratch): PDG_ERR_STATE inside a frame.  Synchronises. */
 pdg_status pdg_precondition(pdg_ctx* ctx, int level, const float* g, float* out, void* cuda_stream);
 
-/* Debug flags (bitwise or), applied to the following steps without re-capturing the step:
- * PDG_DEBUG_KEEP_PGRAD keeps the preconditioned gradient of each step readable as
- * PDG_BUF_PGRAD; PDG_DEBUG_COUNT_NN counts the squared distances the nearest-neighbour search
- * evaluates (PDG_BUF_COUNTERS[0]; one warp-aggregated atomic per query warp, so leave it off
- * while timing).  Unknown bits: PDG_ERR_INVALID.  Synchronises the device. */
+/* Debug flags (bitwise or), applied to the following steps: PDG_DEBUG_KEEP_PGRAD keeps the
+ * preconditioned gradient of each step readable as PDG_BUF_PGRAD; PDG_DEBUG_COUNT_NN runs the
+ * nearest-neighbour search's counting instance, which counts the squared distances it
+ * evaluates and the queries an exact tie decided (PDG_BUF_COUNTERS, pdg_fit_stats.nn_ties;
+ * slower: leave it off while timing).  Changing PDG_DEBUG_COUNT_NN re-captures the context's
+ * step graph at its next pdg_step; a batch never counts.  Unknown bits: PDG_ERR_INVALID.
+ * Synchronises the device. */
 #define PDG_DEBUG_KEEP_PGRAD 1
 #define PDG_DEBUG_COUNT_NN 2
 pdg_status pdg_set_debug(pdg_ctx* ctx, int flags);

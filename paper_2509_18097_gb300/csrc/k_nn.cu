@@ -22,25 +22,33 @@
 
 namespace pdg {
 
-// Best candidate so far; `tie`: another point had exactly the same squared distance (the
-// lowest index decided), which the step reports as a count.
+// Best candidate so far; `tie` (counting instance only): another point had exactly the same
+// squared distance (the lowest index decided), which the step reports as a count.
 struct Best {
   float d2;
   int idx;
   bool tie;
 };
 
+// COUNT: the instance used when the context counts (PDG_DEBUG_COUNT_NN); it also tracks
+// exact ties.  The two instances take the same minimum.
+template <bool COUNT>
 __device__ __forceinline__ void consider(Best& b, const float4 p, float qx, float qy, float qz) {
   const float d2 = sqdist(qx, qy, qz, p.x, p.y, p.z);
   if (d2 <= b.d2) {  // rarely taken; the index decides only between equal distances
     const int id = __float_as_int(p.w);
-    if (d2 < b.d2) {
+    if (COUNT) {
+      if (d2 < b.d2) {
+        b.d2 = d2;
+        b.idx = id;
+        b.tie = false;
+      } else if (id != b.idx) {
+        b.tie = true;
+        b.idx = min(b.idx, id);
+      }
+    } else if (d2 < b.d2 || id < b.idx) {
       b.d2 = d2;
       b.idx = id;
-      b.tie = false;
-    } else if (id != b.idx) {
-      b.tie = true;
-      b.idx = min(b.idx, id);
     }
   }
 }
@@ -101,9 +109,7 @@ __device__ __forceinline__ float axis_lb(const FaceBounds& f, int a, int d) {
 
 // Resolves a query item of a job into its point, grid and set.
 // items [0, Q): forward queries in moving-grid order; [Q, Q + 2M): reverse queries
-// (set 0 then set 1) in target-grid order.  (The forward pass of the step takes its queries
-// in the finest level's cell order instead, resolve_fwd, so that it does not wait for the
-// moving grid.)
+// (set 0 then set 1) in target-grid order.
 struct QueryRef {
   float x, y, z;
   int id;    // Q index (forward) or target index (reverse)
@@ -129,22 +135,11 @@ __device__ __forceinline__ QueryRef resolve(const Job& J, int item) {
   return q;
 }
 
-// forward query `item` of the step's forward pass: point xs[item] of the finest level's cell
-// order, at its deformed position
-__device__ __forceinline__ QueryRef resolve_fwd(const Job& J, int item) {
-  QueryRef q;
-  q.id = __float_as_int(__ldg(&J.lev[J.L - 1].xs[item].w));
-  const float4 p = J.y[q.id];
-  q.x = p.x; q.y = p.y; q.z = p.z;
-  q.fwd = true;
-  q.set = 0;
-  return q;
-}
-
 // The loss term phi(s) = s e^{-alpha s} and the gradient 2 phi'(s) (a - b) of a matched
 // pair (Sec. 3.4); phi'(s) = e^{-alpha s}(1 - alpha s), or e^{-alpha s} with the stop-gradient.
+template <bool COUNT>
 __device__ __forceinline__ void finalize(const Job& J, const QueryRef& q, const Best& b) {
-  if (b.tie) atomicAdd(J.counters + CNT_NN_TIES, 1ull);
+  if (COUNT && b.tie) atomicAdd(J.counters + CNT_NN_TIES, 1ull);
   if (b.idx == 0x7fffffff || !(b.d2 < FLT_MAX)) {  // nothing found (non-finite coordinates)
     if (q.fwd) {
       J.loss_fwd[q.id] = __int_as_float(0x7fc00000);
@@ -181,15 +176,15 @@ __device__ __forceinline__ void finalize(const Job& J, const QueryRef& q, const 
 
 // ------------------------------------------------------------------------------ shells
 
+template <bool COUNT>
 __device__ __forceinline__ void scan_range(const CellGrid& g, int s, int e, float qx, float qy, float qz, Best& b,
                                            int& nc) {
-  nc += e - s;
-  for (int k = s; k < e; ++k) consider(b, __ldg(g.pts + k), qx, qy, qz);
+  if (COUNT) nc += e - s;
+  for (int k = s; k < e; ++k) consider<COUNT>(b, __ldg(g.pts + k), qx, qy, qz);
 }
 
-// adds the candidate counts of the lanes of one job to its counter (profiling only)
+// adds the candidate counts of the lanes of one job to its counter (counting instance)
 __device__ __forceinline__ void count_candidates(const Job& J, int j, int nc) {
-  if (!J.count_nn) return;
   const unsigned act = __activemask();
   const unsigned same = __match_any_sync(act, j);
   const unsigned s = __reduce_add_sync(same, (unsigned)nc);
@@ -200,6 +195,7 @@ __device__ __forceinline__ void count_candidates(const Job& J, int j, int nc) {
 // y/z boundary over the x range [cx - r, cx + r], the others only at x = cx -/+ r.  Cells
 // whose lower bound is above min(cap, best so far) are skipped (strictly above: an equal
 // distance with a lower index must still be seen).
+template <bool COUNT>
 __device__ __forceinline__ void scan_shell_row(const CellGrid& g, int base, int G, int cx, int cy, int cz, int r,
                                                int dy, int dz, float qx, float qy, float qz, const FaceBounds& fb,
                                                float cap, Best& b, int& nc) {
@@ -213,30 +209,26 @@ __device__ __forceinline__ void scan_shell_row(const CellGrid& g, int base, int 
     int x0 = max(cx - r, 0), x1 = min(cx + r, G - 1);
     while (x0 < cx && lyz + axis_lb(fb, 0, x0 - cx) > lim) ++x0;
     while (x1 > cx && lyz + axis_lb(fb, 0, x1 - cx) > lim) --x1;
-    scan_range(g, __ldg(g.off + rk + x0), __ldg(g.off + rk + x1 + 1), qx, qy, qz, b, nc);
+    scan_range<COUNT>(g, __ldg(g.off + rk + x0), __ldg(g.off + rk + x1 + 1), qx, qy, qz, b, nc);
   } else {
     if (cx - r >= 0 && !(lyz + axis_lb(fb, 0, -r) > fminf(cap, b.d2)))
-      scan_range(g, __ldg(g.off + rk + cx - r), __ldg(g.off + rk + cx - r + 1), qx, qy, qz, b, nc);
+      scan_range<COUNT>(g, __ldg(g.off + rk + cx - r), __ldg(g.off + rk + cx - r + 1), qx, qy, qz, b, nc);
     if (cx + r < G && !(lyz + axis_lb(fb, 0, r) > fminf(cap, b.d2)))
-      scan_range(g, __ldg(g.off + rk + cx + r), __ldg(g.off + rk + cx + r + 1), qx, qy, qz, b, nc);
+      scan_range<COUNT>(g, __ldg(g.off + rk + cx + r), __ldg(g.off + rk + cx + r + 1), qx, qy, qz, b, nc);
   }
 }
 
 // ------------------------------------------------------------------------------ thread pass
 
-// mode 0: every query of the step (items of ST_NNQ, as `resolve` numbers them); mode 1: the
-// forward queries only, in cell order (needs the target grid, not the moving one); mode 2:
-// the reverse queries only (needs the moving grid).  Hard-list items keep resolve's numbering.
-__global__ void __launch_bounds__(256) k_nn(const Plan* __restrict__ P, int mode) {
+template <bool COUNT>
+__global__ void __launch_bounds__(256) k_nn(const Plan* __restrict__ P) {
   const int nj = P->n_jobs;
-  const int st = mode == 1 ? ST_Q : mode == 2 ? ST_NNR : ST_NNQ;
-  const int total = P->pre[st][nj];
+  const int total = P->pre[ST_NNQ][nj];
   for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
-    const int j = find_job(P->pre[st], nj, it);
+    const int j = find_job(P->pre[ST_NNQ], nj, it);
     const Job& J = *P->jobs[j];
-    int item = it - P->pre[st][j];
-    if (mode == 2) item += J.Q;
-    const QueryRef q = mode == 1 ? resolve_fwd(J, item) : resolve(J, item);
+    const int item = it - P->pre[ST_NNQ][j];
+    const QueryRef q = resolve(J, item);
     const CellGrid& g = q.fwd ? J.tgt : J.mov;
     const int G = 1 << g.bits;
     const int base = q.set * G * G * G;
@@ -265,11 +257,11 @@ __global__ void __launch_bounds__(256) k_nn(const Plan* __restrict__ P, int mode
     const FaceBounds fb = face_bounds(g, q.x, q.y, q.z, cx, cy, cz);
     {
       int rk = base + row_key(cy, cz, g.bits);
-      scan_range(g, __ldg(g.off + rk + cx), __ldg(g.off + rk + cx + 1), q.x, q.y, q.z, b, nc);
+      scan_range<COUNT>(g, __ldg(g.off + rk + cx), __ldg(g.off + rk + cx + 1), q.x, q.y, q.z, b, nc);
       if (cx > 0 && !(axis_lb(fb, 0, -1) > b.d2))
-        scan_range(g, __ldg(g.off + rk + cx - 1), __ldg(g.off + rk + cx), q.x, q.y, q.z, b, nc);
+        scan_range<COUNT>(g, __ldg(g.off + rk + cx - 1), __ldg(g.off + rk + cx), q.x, q.y, q.z, b, nc);
       if (cx < G - 1 && !(axis_lb(fb, 0, 1) > b.d2))
-        scan_range(g, __ldg(g.off + rk + cx + 1), __ldg(g.off + rk + cx + 2), q.x, q.y, q.z, b, nc);
+        scan_range<COUNT>(g, __ldg(g.off + rk + cx + 1), __ldg(g.off + rk + cx + 2), q.x, q.y, q.z, b, nc);
       // the other 8 x-rows: the 4 sharing a face with the query's row, then the 4 diagonal
       for (int k = 0; k < 8; ++k) {
         int dy, dz;
@@ -287,7 +279,7 @@ __global__ void __launch_bounds__(256) k_nn(const Plan* __restrict__ P, int mode
         const int x0 = cx > 0 && !(lyz + axis_lb(fb, 0, -1) > b.d2) ? cx - 1 : cx;
         const int x1 = cx < G - 1 && !(lyz + axis_lb(fb, 0, 1) > b.d2) ? cx + 1 : cx;
         rk = base + row_key(yy, zz, g.bits);
-        scan_range(g, __ldg(g.off + rk + x0), __ldg(g.off + rk + x1 + 1), q.x, q.y, q.z, b, nc);
+        scan_range<COUNT>(g, __ldg(g.off + rk + x0), __ldg(g.off + rk + x1 + 1), q.x, q.y, q.z, b, nc);
       }
     }
     int r = 1;
@@ -296,18 +288,15 @@ __global__ void __launch_bounds__(256) k_nn(const Plan* __restrict__ P, int mode
       ++r;
       for (int dz = -r; dz <= r; ++dz)
         for (int dy = -r; dy <= r; ++dy)
-          scan_shell_row(g, base, G, cx, cy, cz, r, dy, dz, q.x, q.y, q.z, fb, FLT_MAX, b, nc);
+          scan_shell_row<COUNT>(g, base, G, cx, cy, cz, r, dy, dz, q.x, q.y, q.z, fb, FLT_MAX, b, nc);
       done = b.d2 < outside_bound2(g, q.x, q.y, q.z, cx, cy, cz, r);
     }
-    count_candidates(J, j, nc);
+    if (COUNT) count_candidates(J, j, nc);
     if (done) {
-      finalize(J, q, b);
+      finalize<COUNT>(J, q, b);
     } else {  // ring reached in the low 16 bits, the tie flag above them
-      // the warp pass resolves its items with `resolve`; a forward query taken in cell order
-      // is passed as the negative of its point index plus one
-      const int hitem = mode == 1 ? -(q.id + 1) : item;
       const int slot = atomicAdd(J.hard_count, 1);
-      J.hard[slot] = make_int4(hitem, r | (b.tie ? 0x10000 : 0), __float_as_int(b.d2), b.idx);
+      J.hard[slot] = make_int4(item, r | (COUNT && b.tie ? 0x10000 : 0), __float_as_int(b.d2), b.idx);
     }
   }
 }
@@ -319,6 +308,7 @@ __device__ __forceinline__ unsigned long long pack(const Best& b) {
 }
 
 // lexicographic (d2, idx) minimum over the warp; every lane receives it
+template <bool COUNT>
 __device__ __forceinline__ Best warp_min(const Best& b) {
   unsigned long long m = pack(b);
 #pragma unroll
@@ -331,10 +321,11 @@ __device__ __forceinline__ Best warp_min(const Best& b) {
   r.idx = (int)(unsigned)(m & 0xffffffffu);
   // an exact tie: a lane saw a tie at the minimum, or another lane's best has the same
   // distance with another index
-  r.tie = __any_sync(0xffffffffu, b.d2 == r.d2 && (b.tie || b.idx != r.idx));
+  r.tie = COUNT && __any_sync(0xffffffffu, b.d2 == r.d2 && (b.tie || b.idx != r.idx));
   return r;
 }
 
+template <bool COUNT>
 __global__ void __launch_bounds__(256) k_nn_hard(const Plan* __restrict__ P) {
   __shared__ int hpre[MAXJ + 1];
   const int nj = P->n_jobs;
@@ -360,16 +351,7 @@ __global__ void __launch_bounds__(256) k_nn_hard(const Plan* __restrict__ P) {
     }
     const Job& J = *P->jobs[lo];
     const int4 h = J.hard[w - hpre[lo]];
-    QueryRef q;
-    if (h.x < 0) {  // a forward query by point index
-      q.id = -h.x - 1;
-      const float4 p = J.y[q.id];
-      q.x = p.x; q.y = p.y; q.z = p.z;
-      q.fwd = true;
-      q.set = 0;
-    } else {
-      q = resolve(J, h.x);
-    }
+    const QueryRef q = resolve(J, h.x);
     const CellGrid& g = q.fwd ? J.tgt : J.mov;
     const int G = 1 << g.bits;
     const int base = q.set * G * G * G;
@@ -391,25 +373,32 @@ __global__ void __launch_bounds__(256) k_nn_hard(const Plan* __restrict__ P) {
     for (int r = (h.y & 0xffff) + 1; r <= NN_RMAX && !done; ++r) {
       const int side = 2 * r + 1;
       for (int ri = lane; ri < side * side; ri += 32)
-        scan_shell_row(g, base, G, cx, cy, cz, r, ri % side - r, ri / side - r, q.x, q.y, q.z, fb, best.d2, b, nc);
-      best = warp_min(b);
+        scan_shell_row<COUNT>(g, base, G, cx, cy, cz, r, ri % side - r, ri / side - r, q.x, q.y, q.z, fb, best.d2,
+                              b, nc);
+      best = warp_min<COUNT>(b);
       done = best.d2 < outside_bound2(g, q.x, q.y, q.z, cx, cy, cz, r);
     }
     if (!done) {  // exhaustive scan of the set
       const int s = __ldg(g.off + base), e = __ldg(g.off + base + G * G * G);
-      for (int k = s + lane; k < e; k += 32) consider(b, __ldg(g.pts + k), q.x, q.y, q.z);
-      nc += (e - s + 31 - lane) / 32;
-      best = warp_min(b);
+      for (int k = s + lane; k < e; k += 32) consider<COUNT>(b, __ldg(g.pts + k), q.x, q.y, q.z);
+      if (COUNT) nc += (e - s + 31 - lane) / 32;
+      best = warp_min<COUNT>(b);
     }
-    if (J.count_nn) {
+    if (COUNT) {
       const unsigned s = __reduce_add_sync(0xffffffffu, (unsigned)nc);
       if (lane == 0) atomicAdd(J.counters + CNT_NN_CANDIDATES, (unsigned long long)s);
     }
-    if (lane == 0) finalize(J, q, best);
+    if (lane == 0) finalize<COUNT>(J, q, best);
   }
 }
 
-void launch_nn(const Plan* P, int grid, cudaStream_t s, int mode) { k_nn<<<grid, 256, 0, s>>>(P, mode); }
-void launch_nn_hard(const Plan* P, int grid, cudaStream_t s) { k_nn_hard<<<grid, 256, 0, s>>>(P); }
+void launch_nn(const Plan* P, int grid, cudaStream_t s, bool count) {
+  if (count) k_nn<true><<<grid, 256, 0, s>>>(P);
+  else k_nn<false><<<grid, 256, 0, s>>>(P);
+}
+void launch_nn_hard(const Plan* P, int grid, cudaStream_t s, bool count) {
+  if (count) k_nn_hard<true><<<grid, 256, 0, s>>>(P);
+  else k_nn_hard<false><<<grid, 256, 0, s>>>(P);
+}
 
 }  // namespace pdg

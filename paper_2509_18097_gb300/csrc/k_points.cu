@@ -36,7 +36,6 @@ __global__ void k_plan(Plan* P) {
     const int G = 1 << J->mov.bits;
     cnt[ST_Q][j] = J->Q;
     cnt[ST_NNQ][j] = J->Q + 2 * J->M;
-    cnt[ST_NNR][j] = 2 * J->M;
     cnt[ST_E][j] = J->E;
     cnt[ST_MOVCH][j] = (2 * G * G * G + SCAN_CHUNK - 1) / SCAN_CHUNK;
     int a = 0, t = 0, p3 = 0, cols = 0, ad = 0;
@@ -47,16 +46,15 @@ __global__ void k_plan(Plan* P) {
     int na_l[MAXL], ne_l[MAXL];
 #pragma unroll
     for (int l = 0; l < MAXL; ++l) na_l[l] = l < L ? *J->lev[l].n_active : 0;
-    // every point adds one term to each of its 8 interpolation corners (one for n = 1)
 #pragma unroll
-    for (int l = 0; l < MAXL; ++l) ne_l[l] = l < L ? (J->lev[l].n > 1 ? 8 : 1) * J->Q : 0;
+    for (int l = 0; l < MAXL; ++l) ne_l[l] = na_l[l] > 0 ? J->lev[l].act_ptr[na_l[l]] : 0;
 #pragma unroll
     for (int l = 0; l < MAXL; ++l) {
       if (l >= L) break;
-      // adjoint (in blocks of 8 warps): 2^adj_lg lanes per row, 8 to 16 terms per lane
-      // (a row holds one term per point in the 8 cells around its vertex: a few dozen on
+      // adjoint (in blocks of 8 warps): 2^adj_lg lanes per row, 8 to 16 entries per lane
+      // (a row holds one entry per point in the 8 cells around its vertex: a few dozen on
       // fine levels, thousands on coarse ones), so a warp sums 32 >> adj_lg rows; rows of
-      // 512 terms or more on average (adj_lg = 6) get a whole block each
+      // 512 entries or more on average (adj_lg = 6) get a whole block each
       Level& lv = J->lev[l];
       const int na = na_l[l];
       const int ne = ne_l[l];

@@ -9,8 +9,9 @@ void launch_plan(Plan* P, cudaStream_t s);
 void launch_interp(const Plan* P, int grid, cudaStream_t s, int bump);
 void launch_mov_scan(const Plan* P, int grid, cudaStream_t s);
 void launch_mov_scatter(const Plan* P, int grid, cudaStream_t s);
-void launch_nn(const Plan* P, int grid, cudaStream_t s, int mode);  // 1: forward queries, 2: reverse
-void launch_nn_hard(const Plan* P, int grid, cudaStream_t s);
+// count: the instance that counts candidates and exact ties
+void launch_nn(const Plan* P, int grid, cudaStream_t s, bool count);
+void launch_nn_hard(const Plan* P, int grid, cudaStream_t s, bool count);
 void launch_iso_edges(const Plan* P, int grid, cudaStream_t s);
 void launch_assemble(const Plan* P, int grid, cudaStream_t s);
 void launch_adjoint(const Plan* P, int grid, cudaStream_t s);

@@ -58,15 +58,18 @@ struct Level {
   float* mu;      // [n] eigenvalues 4 sin^2(pi k / 2n) of the 1-D path Laplacian
   float2* tw;     // [n] FFT twiddles exp(-2 pi i k / n)
   float2* tw4;    // [n] DCT twiddles exp(-i pi k / 2n)
-  // the query points sorted by the level's cell, built once per frame (x is fixed in a frame):
-  // cell c = (iz (n-1) + iy) (n-1) + ix holds the points whose interpolation cell it is
-  // (n = 1: one cell holding every point)
+  // point -> vertex interpolation lists, built once per frame (x is fixed in a frame)
+  int* cnt;       // [n3] per-vertex entry counts (zero between builds)
+  int* rowptr;    // [n3 + 1]
+  int* flag;      // [n3 + 1] active-vertex flags, then their exclusive prefix
+  int* act_v;     // [cap] active vertices (ascending)
+  int* act_ptr;   // [cap + 1] entry range of each active vertex
+  int2* ent;      // [8 Q] entries: (point, bits of the trilinear weight / L)
+  // finest level only: the query points in cell order, (iz (n-1) + iy)(n-1) + ix (per frame)
   int* ccnt;      // [cells] points per cell (zero between builds)
   int* coff;      // [cells + 1] exclusive prefix of ccnt
   int* ckey;      // [Q] cell of each point (scratch of the build)
-  float4* xs;     // [Q] points in cell order: (fx, fy, fz, point index bits), f the in-cell fraction
-  int* flag;      // [n3 + 1] active-vertex flags (corner of a non-empty cell), then their prefix
-  int* act_v;     // [cap] active vertices (ascending)
+  float4* xs;     // [Q] points in cell order: (fx, fy, fz, point index bits)
   int* n_active;  // device scalar
   int* csum;      // scan scratch
   int adj_lg;     // adjoint: log2 of the lanes per row, 6 = a block per row (set by the plan kernel)
@@ -122,7 +125,7 @@ struct Job {
 
 enum Counter { CNT_NN_CANDIDATES = 0, CNT_NN_TIES = 1, CNT_NN_HARD = 2 };
 
-enum Stage { ST_Q = 0, ST_NNQ, ST_NNR, ST_E, ST_MOVCH, ST_ADJ, ST_TILE, ST_JOB, ST_LOSSCH, ST_PLANE, ST_COL, ST_ADAM, NSTAGE };
+enum Stage { ST_Q = 0, ST_NNQ, ST_E, ST_MOVCH, ST_ADJ, ST_TILE, ST_JOB, ST_LOSSCH, ST_PLANE, ST_COL, ST_ADAM, NSTAGE };
 
 struct Plan {
   int n_jobs;

@@ -135,8 +135,8 @@ struct Layout {
   size_t total = 0;
   size_t job, plan, flag, stage, op_job, op_plan;
   struct Lv {
-    size_t theta, theta_t, m, v, g, tmp, zmask, piv, piv_slow, mu, tw, tw4, ccnt, coff, ckey, xs, flag, act_v, n_active,
-        csum;
+    size_t theta, theta_t, m, v, g, tmp, zmask, piv, piv_slow, mu, tw, tw4, cnt, rowptr, flag, act_v, act_ptr, ent, ccnt,
+        coff, ckey, xs, n_active, csum;
     int cap;
   } lv[MAXL];
   size_t x, y, gfwd, gy, zq, uq, gz, acc, loss_fwd, loss_rev, loss_iso, nn_fwd, nn_rev, edge_d, edges, e_prev, v2e_ptr, v2e;
@@ -174,13 +174,18 @@ Layout make_layout(const pdg_config& c, int V, int E, int max_pts) {
     v.mu = a.take<float>(n);
     v.tw = a.take<float2>(n);
     v.tw4 = a.take<float2>(n);
-    const size_t cells = n > 1 ? (n - 1) * (n - 1) * (n - 1) : 1;
-    v.ccnt = a.take<int>(cells);
-    v.coff = a.take<int>(cells + 1);
-    v.ckey = a.take<int>(Q);
-    v.xs = a.take<float4>(Q);
+    v.cnt = a.take<int>(n3);
+    v.rowptr = a.take<int>(n3 + 1);
     v.flag = a.take<int>(n3 + 1);
     v.act_v = a.take<int>(v.cap);
+    v.act_ptr = a.take<int>(v.cap + 1);
+    v.ent = a.take<int2>(8 * (size_t)Q);
+    const bool fin = l == c.n_levels - 1;  // the cell order is kept for the finest level only
+    const size_t cells = fin ? (n > 1 ? (n - 1) * (n - 1) * (n - 1) : 1) : 1;
+    v.ccnt = a.take<int>(cells);
+    v.coff = a.take<int>(cells + 1);
+    v.ckey = a.take<int>(fin ? Q : 1);
+    v.xs = a.take<float4>(fin ? Q : 1);
     v.n_active = a.take<int>(1);
     v.csum = a.take<int>((n3 + 1) / SCAN_CHUNK + 2);
   }
@@ -275,35 +280,40 @@ pdg_status load_points(pdg_ctx* c, const float* xyz, int n, float4* dst, cudaStr
   return c->cuda(cudaGetLastError(), "pack points");
 }
 
+// Copies the host mirror of the job record to the device.  The mirror does not hold what the
+// plan kernel writes into the device record (each level's adjoint lanes per row), so the
+// plan of the context, and of any batch holding it, is recomputed before the next step.
 pdg_status upload_job(pdg_ctx* c, cudaStream_t s) {
   CU(c, cudaMemcpyAsync(c->dJ, &c->h, sizeof(Job), cudaMemcpyHostToDevice, s));
+  c->plan_stale = true;
+  ++c->frame_gen;
   return PDG_OK;
 }
 
 // The step as an explicit list of stages; the graph capture and the profiling path launch
 // exactly the same sequence.
-const char* const STAGE_NAMES[] = {"interp",     "nn_fwd",     "mov_scan", "mov_scatter", "nn_rev",
-                                   "nn_hard",    "iso_edges",  "assemble", "adjoint",     "sob_xy_fwd",
-                                   "sob_z",      "sob_xy_inv", "adam",     "sobolev_256", "loss"};
+const char* const STAGE_NAMES[] = {"interp",     "mov_scan",   "mov_scatter", "nn",          "nn_hard",
+                                   "iso_edges",  "assemble",   "adjoint",     "sob_xy_fwd",  "sob_z",
+                                   "sob_xy_inv", "adam",       "sobolev_256", "loss"};
 constexpr int N_STAGES = sizeof(STAGE_NAMES) / sizeof(STAGE_NAMES[0]);
 enum StageIndex {
-  S_INTERP = 0, S_NN_FWD, S_MOV_SCAN, S_MOV_SCATTER, S_NN_REV, S_NN_HARD, S_ISO, S_ASSEMBLE, S_ADJOINT,
+  S_INTERP = 0, S_MOV_SCAN, S_MOV_SCATTER, S_NN, S_NN_HARD, S_ISO, S_ASSEMBLE, S_ADJOINT,
   S_SOB_XY_FWD, S_SOB_Z, S_SOB_XY_INV, S_ADAM, S_SOB_256, S_LOSS
 };
 
 // Stage i of a step; bump: the job_bump mode of the interpolation stage (1: optimisation
-// step, 2: evaluation).  The plan's item prefixes must be current (refresh_plan).
-void launch_stage(int i, const Plan* plan, int nmax, int sms, cudaStream_t s, int bump = 1) {
+// step, 2: evaluation); count: the nearest-neighbour instances that count candidates and
+// exact ties.  The plan's item prefixes must be current (refresh_plan).
+void launch_stage(int i, const Plan* plan, int nmax, int sms, cudaStream_t s, int bump = 1, bool count = false) {
   const int grid = sms * 8;
   const int smem = sobolev_smem_bytes(nmax);
   const int tiles_per_sm = std::max(1, std::min(4, (227 * 1024) / std::max(smem, 1)));
   switch (i) {
     case S_INTERP: launch_interp(plan, grid, s, bump); break;
-    case S_NN_FWD: launch_nn(plan, grid * 2, s, 1); break;
     case S_MOV_SCAN: launch_mov_scan(plan, sms * 2, s); break;
     case S_MOV_SCATTER: launch_mov_scatter(plan, grid, s); break;
-    case S_NN_REV: launch_nn(plan, grid * 2, s, 2); break;
-    case S_NN_HARD: launch_nn_hard(plan, sms * 4, s); break;
+    case S_NN: launch_nn(plan, grid * 2, s, count); break;
+    case S_NN_HARD: launch_nn_hard(plan, sms * 4, s, count); break;
     case S_ISO: launch_iso_edges(plan, grid, s); break;
     case S_ASSEMBLE: launch_assemble(plan, grid, s); break;
     case S_ADJOINT: launch_adjoint(plan, grid * 2, s); break;
@@ -324,9 +334,8 @@ void launch_stage(int i, const Plan* plan, int nmax, int sms, cudaStream_t s, in
 }
 constexpr int ST_SOB_FIRST = S_SOB_XY_FWD, ST_SOB_LAST = S_SOB_256;  // preconditioner and Adam stages
 
-// Captures one step.  Two branches: the forward nearest-neighbour pass (it needs the
-// per-frame target grid and the deformed points, not the moving grid) and the isometry
-// kernel run beside the moving grid's sort and the reverse pass; the loss reduction runs
+// Captures one step.  Two branches: the isometry kernel runs beside the moving grid's sort
+// and the nearest-neighbour passes (it needs only the deformed points), the loss reduction
 // beside the adjoint and the preconditioner (nothing downstream reads it).
 pdg_status capture_step(pdg_ctx* c, const Plan* plan, int nmax, cudaStream_t cap, cudaStream_t cap2,
                         cudaGraphExec_t* out, std::string* err, int sms, int* n_kernels = nullptr) {
@@ -343,17 +352,17 @@ pdg_status capture_step(pdg_ctx* c, const Plan* plan, int nmax, cudaStream_t cap
     for (auto& x : ev) cudaEventDestroy(x);
     return PDG_ERR_CUDA;
   }
+  const bool count = c && c->h.count_nn;  // a batch graph never counts
   launch_stage(S_INTERP, plan, nmax, sms, cap);  // starts the step of every job
   cudaEventRecord(ev[0], cap);
   cudaStreamWaitEvent(cap2, ev[0], 0);
-  launch_stage(S_NN_FWD, plan, nmax, sms, cap2);
   launch_stage(S_ISO, plan, nmax, sms, cap2);
   cudaEventRecord(ev[1], cap2);
   launch_stage(S_MOV_SCAN, plan, nmax, sms, cap);
   launch_stage(S_MOV_SCATTER, plan, nmax, sms, cap);
-  launch_stage(S_NN_REV, plan, nmax, sms, cap);
+  launch_stage(S_NN, plan, nmax, sms, cap, 1, count);
+  launch_stage(S_NN_HARD, plan, nmax, sms, cap, 1, count);
   cudaStreamWaitEvent(cap, ev[1], 0);
-  launch_stage(S_NN_HARD, plan, nmax, sms, cap);
   launch_stage(S_ASSEMBLE, plan, nmax, sms, cap);
   cudaEventRecord(ev[2], cap);
   cudaStreamWaitEvent(cap2, ev[2], 0);
@@ -573,12 +582,16 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
     lv.mu = (float*)P(o.mu);
     lv.tw = (float2*)P(o.tw);
     lv.tw4 = (float2*)P(o.tw4);
+    lv.cnt = (int*)P(o.cnt);
+    lv.rowptr = (int*)P(o.rowptr);
+    lv.flag = (int*)P(o.flag);
+    lv.act_v = (int*)P(o.act_v);
+    lv.act_ptr = (int*)P(o.act_ptr);
+    lv.ent = (int2*)P(o.ent);
     lv.ccnt = (int*)P(o.ccnt);
     lv.coff = (int*)P(o.coff);
     lv.ckey = (int*)P(o.ckey);
     lv.xs = (float4*)P(o.xs);
-    lv.flag = (int*)P(o.flag);
-    lv.act_v = (int*)P(o.act_v);
     lv.n_active = (int*)P(o.n_active);
     lv.csum = (int*)P(o.csum);
     c->nmax = std::max(c->nmax, n);
@@ -683,7 +696,13 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
 pdg_status pdg_set_debug(pdg_ctx* c, int flags) {
   if (!c || (flags & ~(PDG_DEBUG_KEEP_PGRAD | PDG_DEBUG_COUNT_NN))) return PDG_ERR_INVALID;
   c->h.keep_pgrad = (flags & PDG_DEBUG_KEEP_PGRAD) ? 1 : 0;
-  c->h.count_nn = (flags & PDG_DEBUG_COUNT_NN) ? 1 : 0;
+  const int count = (flags & PDG_DEBUG_COUNT_NN) ? 1 : 0;
+  if (count != c->h.count_nn && c->gexec) {  // the step graph holds the other NN instances
+    if (cudaDeviceSynchronize() != cudaSuccess) return PDG_ERR_CUDA;
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  c->h.count_nn = count;
   return upload_job(c, 0) == PDG_OK ? c->cuda(cudaDeviceSynchronize(), "set_debug") : PDG_ERR_CUDA;
 }
 
@@ -771,7 +790,7 @@ pdg_status pdg_profile_step(pdg_ctx* c, int n_steps, double* stage_ms, void* cud
   for (int k = 0; k < n_steps && st == PDG_OK; ++k) {
     for (int i = 0; i < N_STAGES; ++i) {
       cudaEventRecord(ev[i], s);
-      launch_stage(i, c->dplan, c->nmax, c->sms, s);
+      launch_stage(i, c->dplan, c->nmax, c->sms, s, 1, c->h.count_nn != 0);
     }
     cudaEventRecord(ev[N_STAGES], s);
     st = c->cuda(cudaEventSynchronize(ev[N_STAGES]), "profile step");
@@ -811,7 +830,7 @@ pdg_status pdg_end_frame(pdg_ctx* c, pdg_fit_stats* stats, void* cuda_stream) {
     stats->iso = loss[3];
     stats->n_steps = c->steps_in_frame;
     stats->status = st;
-    stats->nn_ties = c->steps_in_frame > 0 ? (int)std::min<unsigned long long>(cnt[CNT_NN_TIES], 0x7fffffff) : 0;
+    stats->nn_ties = !J.count_nn ? -1 : c->steps_in_frame > 0 ? (int)std::min<unsigned long long>(cnt[CNT_NN_TIES], 0x7fffffff) : 0;
   }
   if (st != PDG_OK) c->err = "a loss became NaN or Inf during the frame";
   return st;
@@ -959,7 +978,7 @@ pdg_status pdg_eval(pdg_ctx* c, double* loss, void* cuda_stream) {
   cudaStream_t s = (cudaStream_t)cuda_stream;
   TRY(refresh_plan(c, s));
   for (int i = 0; i < N_STAGES; ++i)  // no preconditioner, no Adam, no step count
-    if (i < ST_SOB_FIRST || i > ST_SOB_LAST) launch_stage(i, c->dplan, c->nmax, c->sms, s, 2);
+    if (i < ST_SOB_FIRST || i > ST_SOB_LAST) launch_stage(i, c->dplan, c->nmax, c->sms, s, 2, c->h.count_nn != 0);
   CU(c, cudaGetLastError());
   if (loss) {
     CU(c, cudaMemcpyAsync(loss, c->h.loss, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));

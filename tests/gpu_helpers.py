@@ -74,7 +74,7 @@ def is_close(a, b, rtol=RTOL, atol_rel=ATOL_REL):
     return bool(np.all(np.abs(a - b) <= atol_rel * S + rtol * np.abs(b)))
 
 
-def gpu_run(w, cfg_kwargs=None, thetas=None, steps=1, read=True, debug=True):
+def gpu_run(w, cfg_kwargs=None, thetas=None, steps=1, read=True, debug=True, count_nn=False):
     """Runs `steps` iterations of one frame through the C-ABI and reads every buffer."""
     import torch
 
@@ -86,8 +86,8 @@ def gpu_run(w, cfg_kwargs=None, thetas=None, steps=1, read=True, debug=True):
     mp = max(len(w.source), len(w.target))
     ctx = B.pdg_create(cfg, w.template, w.edges, w.source, max_pts=mp)
     try:
-        if debug:
-            B.pdg_set_debug(ctx, True)
+        if debug or count_nn:
+            B.pdg_set_debug(ctx, debug, count_nn=count_nn)
         B.pdg_begin_frame(ctx, w.target)
         if thetas is not None:
             for l, th in enumerate(thetas):

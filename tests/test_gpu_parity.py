@@ -207,7 +207,7 @@ def test_exact_ties_lowest_index():
     tgt = np.concatenate([base, base, base[:100]]).astype(np.float32)  # triplicates
     src = base[:250].astype(np.float32)  # queries coincide with target points (d2 = 0 ties)
     w = synth.Workload("ties", v, e, src, tgt, (4, 8))
-    g = H.gpu_run(w)
+    g = H.gpu_run(w, count_nn=True)
     V = len(v)
     idx, _ = O.nn_bruteforce(g["y"][V:].astype(np.float64), tgt.astype(np.float64))
     assert np.array_equal(g["nn_fwd"][V:], idx)
@@ -234,13 +234,12 @@ def test_outlier_queries_use_the_ring_search():
 
 
 def test_step_graph_kernel_count():
-    """One step of levels up to 128^3 is 16 launches: interpolation (which also starts the
-    step's Adam count), two scan phases and the scatter of the moving grid, the forward and
-    reverse NN passes and the warp pass, isometry, assembly, the two loss kernels, adjoint,
-    the three preconditioner passes and Adam.  The plan's item prefixes are computed outside
-    the step, once per frame."""
+    """One step of levels up to 128^3 is 15 launches: interpolation (which also starts the
+    step's Adam count), two scan phases and the scatter of the moving grid, the two NN
+    passes, isometry, assembly, the two loss kernels, adjoint, the three preconditioner
+    passes and Adam.  The plan's item prefixes are computed outside the step, once per frame."""
     g = H.gpu_run(small_sphere(seed=13), read=False)
-    assert g["kernels_per_step"] == 16
+    assert g["kernels_per_step"] == 15
 
 
 def test_one_step_stagewise_256_level():
@@ -308,3 +307,36 @@ def test_second_frame_through_end_frame(warm):
         B.pdg_destroy(ctx)
     info = H.stagewise(w2, g, H.oracle_cfg(w2))
     print("frame 2", "warm" if warm else "cold", info)
+
+
+def test_counting_instance_mid_frame_matches_default_bitwise():
+    """Switching the nearest-neighbour counting instance on in the middle of a frame
+    (pdg_set_debug re-uploads the job record and re-captures the step) runs the same
+    arithmetic: the next steps are bitwise those of a context that never counted, and the
+    counters hold candidate and warp-pass counts."""
+    from paper_2509_18097_gb300 import binding as B
+
+    w = small_sphere(seed=61)
+    res = []
+    for count in (False, True):
+        ctx = B.pdg_create(B.pdg_config_default(res=w.res), w.template, w.edges, w.source,
+                           max_pts=max(len(w.source), len(w.target)))
+        try:
+            B.pdg_begin_frame(ctx, w.target)
+            B.pdg_step(ctx, 3)
+            B.pdg_set_debug(ctx, False, count_nn=count)
+            B.pdg_step(ctx, 3)
+            cnt = B.pdg_read(ctx, B.BUF_COUNTERS, 0, np.empty(4, np.uint64))
+            B.pdg_set_debug(ctx, False, count_nn=False)
+            B.pdg_step(ctx, 2)
+            out = {"y": B.pdg_read(ctx, B.BUF_Y, 0, np.empty((len(w.template) + len(w.source), 3), np.float32)),
+                   "loss": B.pdg_read(ctx, B.BUF_LOSS, 0, np.empty(4, np.float64))}
+            for l, n in enumerate(w.res):
+                out[l] = B.pdg_read(ctx, B.BUF_THETA, l, np.empty((n**3, 3), np.float32))
+            res.append((out, cnt))
+        finally:
+            B.pdg_destroy(ctx)
+    (a, _), (b, cnt) = res
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    assert int(cnt[0]) >= len(w.template) + len(w.source)  # at least one candidate per forward query
