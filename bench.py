@@ -236,20 +236,23 @@ def run_serving(n_seq=32, n_frames=2, steps=100, rate_hz=100.0, scale=1.0, budge
            "points_per_frame": [int(min(len(f) for s_ in seqs for f in s_.frames)),
                                 int(max(len(f) for s_ in seqs for f in s_.frames))],
            "finest_res": [int(min(s_.res[-1] for s_ in seqs)), int(max(s_.res[-1] for s_ in seqs))]}
-    srv = serve.Server(seqs, steps=steps, budget_bytes=int(budget_gb * 1e9), max_slots=SERVE_SLOTS)
-    b = srv.run(serve.poisson_trace(seqs, rate_hz, seed=1), realtime=True)
-    srv.close()
+    res = {}
+    for order in ("fifo", "size"):
+        srv = serve.Server(seqs, steps=steps, budget_bytes=int(budget_gb * 1e9), max_slots=SERVE_SLOTS, order=order)
+        res[order] = srv.run(serve.poisson_trace(seqs, rate_hz, seed=1), realtime=True)
+        srv.close()
     p = serve.serve_plain(seqs, serve.poisson_trace(seqs, rate_hz, seed=1), steps, realtime=True)
-    for k, r in (("batched", b), ("plain", p)):
+    for k, r in (("batched", res["size"]), ("batched_fifo", res["fifo"]), ("plain", p)):
         out[k] = {"frames_per_s": r["frames_per_s"], "p50_ms": 1e3 * r["p50_s"], "p99_ms": 1e3 * r["p99_s"],
                   "wall_s": r["wall_s"]}
     return out
 
 
 # Live frames of the served runs: enough jobs per batched launch to amortise launches and
-# fill the GPU with small jobs, few enough that frames finish near arrival order (with every
+# fill the GPU with small jobs, few enough that frames do not all share the GPU (with every
 # queued frame admitted at once, an overloaded server shares the GPU between all of them and
-# every frame finishes late).
+# every frame finishes late).  "batched" admits the smallest waiting frames first,
+# "batched_fifo" in arrival order; "plain" runs one frame at a time in arrival order.
 SERVE_SLOTS = 8
 
 
@@ -278,7 +281,7 @@ def run_serving_scale(steps=100, budget_gb=150.0):
     seqs = serving_sequences(64, 10)
     trace_b = [serve.Request(s.sid, k, 0.0) for s in seqs for k in range(len(s.frames))]
     trace_p = [serve.Request(s.sid, k, 0.0) for s in seqs for k in range(len(s.frames))]
-    srv = serve.Server(seqs, steps=steps, budget_bytes=int(budget_gb * 1e9), max_slots=64)
+    srv = serve.Server(seqs, steps=steps, budget_bytes=int(budget_gb * 1e9), max_slots=64, order="size")
     b = srv.run(trace_b, realtime=False)
     srv.close()
     p = serve.serve_plain(seqs, trace_p, steps, realtime=False)
@@ -290,10 +293,11 @@ def run_serving_scale(steps=100, budget_gb=150.0):
                          "budget_gb": budget_gb, "slots": SERVE_SLOTS, "rates": {}}
     for rate in (50.0, 100.0, 200.0, 400.0):
         r = {}
-        for mode in ("batched", "plain"):
+        for mode in ("batched", "batched_fifo", "plain"):
             tr = serve.poisson_trace(seqs, rate, seed=7)
-            if mode == "batched":
-                srv = serve.Server(seqs, steps=steps, budget_bytes=int(budget_gb * 1e9), max_slots=SERVE_SLOTS)
+            if mode != "plain":
+                srv = serve.Server(seqs, steps=steps, budget_bytes=int(budget_gb * 1e9), max_slots=SERVE_SLOTS,
+                                   order="size" if mode == "batched" else "fifo")
                 st = srv.run(tr, realtime=True)
                 srv.close()
             else:

@@ -68,6 +68,13 @@ def poisson_trace(seqs, rate_hz: float, seed: int = 0):
     return order
 
 
+def frame_cost(s: Sequence, frame: int) -> float:
+    """Estimated device bytes of one iteration of a frame: about 200 B per query and target
+    point (evaluation, searches, gradients) and 100 B per grid vertex (adjoint, preconditioner,
+    Adam).  Used only to order admissions."""
+    return 200.0 * (len(s.template) + len(s.source0) + 2 * len(s.frames[frame])) + 100.0 * sum(n**3 for n in s.res)
+
+
 def _percentiles(lat):
     lat = np.asarray(lat)
     return float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
@@ -79,10 +86,12 @@ class Server:
     `chunk` bounds the iterations one batch launch runs, so a frame that arrives while
     others are on the GPU joins them at the next boundary of at most `chunk` iterations
     (its set-up runs on a side stream meanwhile, from host memory); the host stays at most one
-    chunk ahead of the GPU."""
+    chunk ahead of the GPU.  `order` picks which waiting frames fill free slots: "fifo" in
+    arrival order, "size" the smallest estimated work first (frame_cost); either way only
+    the next frame of each sequence is eligible, so a sequence's frames stay in order."""
 
     def __init__(self, seqs, steps: int, budget_bytes: int, max_slots: int = 64, device=None, cfg_kwargs=None,
-                 chunk: int = 4):
+                 chunk: int = 4, order: str = "fifo"):
         import torch
 
         from . import binding as B
@@ -95,6 +104,9 @@ class Server:
         self.budget = budget_bytes
         self.max_slots = max_slots
         self.chunk = max(1, int(chunk))
+        if order not in ("fifo", "size"):
+            raise ValueError("order must be 'fifo' or 'size'")
+        self.order = order
         self.cfg_kwargs = cfg_kwargs or {}
         self.used = 0
         self.ctx = {}  # sid -> context handle
@@ -144,7 +156,14 @@ class Server:
             # set-up runs on the side stream (host target copied by the library), beside the
             # batch's iterations on the main stream
             admitted = False
-            for r in list(arrived):
+            # the next frame of each idle sequence, in the admission order
+            firsts = {}
+            for r in arrived:
+                if r.sid not in busy and (r.sid not in firsts or r.frame < firsts[r.sid].frame):
+                    firsts[r.sid] = r
+            cand = sorted(firsts.values(), key=lambda r: (frame_cost(self.seqs[r.sid], r.frame), r.arrival)
+                          if self.order == "size" else (r.arrival,))
+            for r in cand:
                 if len(live) >= self.max_slots:
                     break
                 if r.sid in busy:

@@ -105,13 +105,16 @@ def seq_set(n_seq=4, n_frames=3):
     return seqs
 
 
-def test_server_results_equal_plain_and_solo():
+@pytest.mark.parametrize("order", ["fifo", "size"])
+def test_server_results_equal_plain_and_solo(order):
+    """Whatever the admission order, every frame's result is bitwise the one the plain
+    one-at-a-time form gives."""
     from paper_2509_18097_gb300 import serve
 
     seqs = seq_set()
     trace_a = serve.poisson_trace(seqs, rate_hz=2000.0, seed=1)
     trace_b = serve.poisson_trace(seqs, rate_hz=2000.0, seed=1)
-    srv = serve.Server(seqs, steps=6, budget_bytes=8 * 1024**3, max_slots=3)
+    srv = serve.Server(seqs, steps=6, budget_bytes=8 * 1024**3, max_slots=3, order=order)
     stats = srv.run(trace_a, realtime=False)
     srv.close()
     plain = serve.serve_plain(seqs, trace_b, steps=6, realtime=False)
