@@ -469,6 +469,80 @@ def adam_update(theta, m, v, g, k, lr, beta1=BETA1, beta2=BETA2, eps=EPS):
 
 
 # ---------------------------------------------------------------------------------------
+# template-mesh optimisation, Sec. 3.4 (surface initialisation loss) and Sec. 3.6
+# ---------------------------------------------------------------------------------------
+
+MESH_LAMBDA = 16.0  # smoothness weight of the mesh preconditioner, Sec. 3.6
+MESH_LR = 1e-4  # fixed learning rate of the mesh vertices, Sec. 3.6
+
+
+def mesh_laplacian(n_verts, edges):
+    """The combinatorial graph Laplacian (degree minus adjacency) of the mesh edges, as a
+    scipy CSR matrix.  Reading: the paper preconditions the mesh vertices following Nicolet
+    et al. (Sec. 3.2, last paragraph) without naming the Laplacian; this is the uniform-weight
+    one, the mesh analogue of the grid Laplacian."""
+    import scipy.sparse as sp
+
+    e = np.asarray(edges, np.int64)
+    A = sp.coo_matrix((np.ones(2 * len(e)), (np.concatenate([e[:, 0], e[:, 1]]), np.concatenate([e[:, 1], e[:, 0]]))),
+                      shape=(n_verts, n_verts)).tocsr()
+    deg = np.asarray(A.sum(1)).ravel()
+    return (sp.diags(deg) - A).tocsr()
+
+
+def mesh_precondition(g, edges, lam):
+    """(I + lam L)^{-2} g per channel with L the mesh Laplacian: two sparse direct solves (a
+    library step).  Reading: the same form as the grids' preconditioner (Sec. 3.2 Eq. 3 with
+    the raw gradient then fed to Adam), with the mesh's Laplacian.  g: [V, C]."""
+    import scipy.sparse as sp
+    from scipy.sparse.linalg import factorized
+
+    g = np.asarray(g, F64)
+    if lam == 0:
+        return g.copy()
+    A = (sp.identity(len(g), format="csc") + lam * mesh_laplacian(len(g), edges)).tocsc()
+    solve = factorized(A)
+    out = np.empty_like(g)
+    for c in range(g.shape[1]):
+        out[:, c] = solve(solve(g[:, c]))
+    return out
+
+
+@dataclasses.dataclass
+class MeshState:
+    """Template-mesh fit: the vertices X_0 being optimised, the keyframe cloud P_0, the edges
+    and Adam state (Sec. 3.4, L_mesh; Sec. 3.6)."""
+
+    X: np.ndarray
+    target: np.ndarray
+    edges: np.ndarray
+    m: np.ndarray
+    v: np.ndarray
+    k: int = 0
+
+
+def mesh_begin(template, target, edges):
+    X = np.asarray(template, F64).copy()
+    return MeshState(X=X, target=np.asarray(target, F64), edges=np.asarray(edges, np.int64), m=np.zeros_like(X),
+                     v=np.zeros_like(X))
+
+
+def mesh_step(st: MeshState, lam=MESH_LAMBDA, lr=MESH_LR, alpha=ALPHA, update=True, cfg: Config | None = None):
+    """One iteration of the template-mesh fit: L_mesh = CD_R(X_0, P_0) (Sec. 3.4) and its
+    gradient with respect to the vertices, preconditioned by (I + lam L_mesh)^{-2}, then Adam
+    with the fixed learning rate (Sec. 3.6).  Returns the loss, gradient and preconditioned
+    gradient (before the update)."""
+    c = cfg or Config()
+    ch = robust_chamfer(st.X, st.target, alpha, c.robust_weight_stopgrad)
+    pg = mesh_precondition(ch["grad_A"], st.edges, lam)
+    out = dict(loss=ch["loss"], grad=ch["grad_A"], pgrad=pg, chamfer=ch, X=st.X.copy())
+    if update:
+        st.k += 1
+        st.X, st.m, st.v = adam_update(st.X, st.m, st.v, pg, st.k, lr, c.beta1, c.beta2, c.eps)
+    return out
+
+
+# ---------------------------------------------------------------------------------------
 # the whole per-iteration step and the per-frame fit
 # ---------------------------------------------------------------------------------------
 

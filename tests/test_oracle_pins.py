@@ -627,3 +627,66 @@ def test_cayley_step_gradient_matches_finite_differences():
     assert checked >= 12
     # both halves of the payload receive gradient
     assert np.abs(base["grads"][1][..., :3]).max() > 0 and np.abs(base["grads"][1][..., 3:]).max() > 0
+
+
+# --------------------------------------------------------------------------------- mesh fit
+
+
+def test_mesh_laplacian_hand_triangle_and_nullspace():
+    e = np.array([[0, 1], [1, 2], [2, 0], [2, 3]])
+    L = O.mesh_laplacian(4, e).toarray()
+    np.testing.assert_array_equal(L, [[2, -1, -1, 0], [-1, 2, -1, 0], [-1, -1, 3, -1], [0, 0, -1, 1]])
+    from paper_2509_18097_gb300 import synth
+
+    v, _, e = synth.icosphere(2)
+    L = O.mesh_laplacian(len(v), e)
+    np.testing.assert_allclose(L @ np.ones(len(v)), 0.0, atol=1e-12)
+    assert abs(L - L.T).max() == 0
+
+
+@pytest.mark.parametrize("k,lam", [(1, 16.0), (5, 0.75), (12, 3.0)])
+def test_mesh_precondition_ring_fourier_mode(k, lam):
+    """On a ring of n vertices the Laplacian's eigenvectors are cos/sin(2 pi k i / n) with
+    eigenvalue 2 - 2 cos(2 pi k / n), so (I + lam L)^{-2} scales them by the closed form."""
+    n = 40
+    i = np.arange(n)
+    e = np.stack([i, (i + 1) % n], 1)
+    g = np.stack([np.cos(2 * np.pi * k * i / n), np.sin(2 * np.pi * k * i / n), 0.5 * np.cos(2 * np.pi * k * i / n)], 1)
+    f = (1 + lam * (2 - 2 * math.cos(2 * math.pi * k / n))) ** -2
+    np.testing.assert_allclose(O.mesh_precondition(g, e, lam), f * g, atol=1e-12)
+
+
+def test_mesh_precondition_identity_sum_symmetry():
+    from paper_2509_18097_gb300 import synth
+
+    v, _, e = synth.icosphere(2)
+    r = rng(50)
+    a, b = r.standard_normal((len(v), 3)), r.standard_normal((len(v), 3))
+    np.testing.assert_array_equal(O.mesh_precondition(a, e, 0.0), a)
+    c = np.ones((len(v), 3)) * 0.3
+    np.testing.assert_allclose(O.mesh_precondition(c, e, 16.0), c, atol=1e-12)  # constants: L c = 0
+    Pa, Pb = O.mesh_precondition(a, e, 16.0), O.mesh_precondition(b, e, 16.0)
+    np.testing.assert_allclose(Pa.sum(0), a.sum(0), rtol=1e-10)
+    assert math.isclose((Pa * b).sum(), (a * Pb).sum(), rel_tol=1e-10)
+
+
+def test_mesh_fit_lowers_the_surface_loss():
+    """Preconditioned Adam on the vertices (lambda = 16, lr = 1e-4, the paper's values) lowers
+    CD_R(X_0, P_0) toward an inflated target, and the first update is Adam's first step in
+    closed form, -lr g / (|g| + eps) of the preconditioned gradient."""
+    from paper_2509_18097_gb300 import synth
+
+    v, _, e = synth.icosphere(2)
+    r = rng(51)
+    P0 = synth.sphere_points(r, 900) * 1.05
+    st = O.mesh_begin(v, P0, e)
+    o = O.mesh_step(st)
+    moved = st.X - o["X"]
+    pg = o["pgrad"]
+    np.testing.assert_allclose(moved, -O.MESH_LR * pg / (np.abs(pg) + O.EPS), rtol=1e-9, atol=1e-18)
+    radius = [np.linalg.norm(st.X, axis=1).mean()]
+    losses = [o["loss"]]
+    for _ in range(40):
+        losses.append(O.mesh_step(st)["loss"])
+        radius.append(np.linalg.norm(st.X, axis=1).mean())
+    assert losses[-1] < losses[0] and np.all(np.diff(radius) > 0)  # the mesh inflates toward P_0
