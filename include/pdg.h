@@ -154,10 +154,13 @@ enum pdg_buffer {
   PDG_BUF_NN_REV = 6,   /* int32 [2][n_tgt]: nearest template vertex / source point of each target point */
   PDG_BUF_LOSS = 7,     /* double [4]: total, cd_mesh, cd_pts, iso of the last step */
   PDG_BUF_SOURCE = 8,   /* current source cloud P_{t-1}, float [n_src][3] */
-  PDG_BUF_COUNTERS = 9  /* uint64 [4] of the last step: squared distances the nearest-neighbour
+  PDG_BUF_COUNTERS = 9, /* uint64 [4] of the last step: squared distances the nearest-neighbour
                            search evaluated and queries decided by an exact tie (both counted
                            only with PDG_DEBUG_COUNT_NN, else 0), queries left to the
                            warp-cooperative ring search, 0 */
+  PDG_BUF_MESH_GRAD = 10, /* dL_mesh/dX of the last pdg_fit_mesh iteration, float [n_verts][3]
+                             (PDG_ERR_STATE before a fit, or once a frame has begun since) */
+  PDG_BUF_MESH_PGRAD = 11 /* the same preconditioned, (I + lambda L)^{-2} dL_mesh/dX */
 };
 pdg_status pdg_read(pdg_ctx* ctx, int which, int level, void* out, size_t out_bytes, void* cuda_stream);
 
@@ -193,6 +196,23 @@ pdg_status pdg_eval(pdg_ctx* ctx, double* loss, void* cuda_stream);
  * step.  g, out: float [res^3][3], host or device.  Only between frames (the level's
  * gradient buffers are used as scratch): PDG_ERR_STATE inside a frame.  Synchronises. */
 pdg_status pdg_precondition(pdg_ctx* ctx, int level, const float* g, float* out, void* cuda_stream);
+
+/* Template-mesh fit (Sec. 3.4, surface initialisation loss; Sec. 3.6): moves the context's
+ * template vertices X (the mesh the next frame starts from; X_0 before the first frame) to
+ * reduce L_mesh = CD_R(X, P_0) against the keyframe cloud p0_xyz ([n_p0][3], host or device,
+ * 1 <= n_p0 <= max_pts), by n_steps iterations of: the exact robust Chamfer search and
+ * gradient (the step's kernels, mesh term only), the gradient preconditioned by
+ * (I + lambda L_mesh)^{-2} with L_mesh the combinatorial graph Laplacian of the mesh edges
+ * (two Chebyshev solves, relative error below 1e-7 in exact arithmetic), then Adam with
+ * learning rate lr (fresh moments each call; beta1, beta2, eps of the context's config).
+ * The paper's values are lambda = 16, lr = 1e-4; lambda >= 0 with lambda times the largest
+ * vertex degree at most 1e5, lr >= 0, n_steps >= 0 (PDG_ERR_INVALID otherwise; n_p0 above
+ * max_pts: PDG_ERR_BUDGET).  Between frames only (PDG_ERR_STATE inside
+ * a frame); the source cloud and the grids are untouched.  stats (may be NULL): loss_total =
+ * cd_mesh = L_mesh of the last iteration (before its update).  Synchronises `cuda_stream`.
+ * PDG_ERR_NONFINITE if a loss was NaN/Inf (the vertices are then as the fit left them). */
+pdg_status pdg_fit_mesh(pdg_ctx* ctx, const float* p0_xyz, int n_p0, int n_steps, float lambda, float lr,
+                        pdg_fit_stats* stats, void* cuda_stream);
 
 /* Debug flags (bitwise or), applied to the following steps: PDG_DEBUG_KEEP_PGRAD keeps the
  * preconditioned gradient of each step readable as PDG_BUF_PGRAD; PDG_DEBUG_COUNT_NN runs the

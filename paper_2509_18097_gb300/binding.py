@@ -19,7 +19,9 @@ MAX_LEVELS = 8
 
 PAYLOAD_DISPLACEMENT, PAYLOAD_CAYLEY = 0, 1
 OK, ERR_INVALID, ERR_OOM, ERR_BUDGET, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE = range(8)
-BUF_THETA, BUF_GRAD, BUF_PGRAD, BUF_Y, BUF_POINT_GRAD, BUF_NN_FWD, BUF_NN_REV, BUF_LOSS, BUF_SOURCE, BUF_COUNTERS = range(10)
+(BUF_THETA, BUF_GRAD, BUF_PGRAD, BUF_Y, BUF_POINT_GRAD, BUF_NN_FWD, BUF_NN_REV, BUF_LOSS, BUF_SOURCE, BUF_COUNTERS,
+ BUF_MESH_GRAD, BUF_MESH_PGRAD) = range(12)
+MESH_LAMBDA, MESH_LR = 16.0, 1e-4  # the paper's mesh smoothness weight and learning rate
 DEBUG_KEEP_PGRAD, DEBUG_COUNT_NN = 1, 2
 
 
@@ -84,6 +86,8 @@ _SIGS = {
     "pdg_set_debug": (C.c_int, [C.c_void_p, C.c_int]),
     "pdg_precondition": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pdg_eval": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
+    "pdg_fit_mesh": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_float, C.c_float, C.POINTER(pdg_fit_stats),
+                               C.c_void_p]),
     "pdg_precondition_static": (C.c_int, [C.c_int, C.c_float, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pdg_profile_stages": (C.c_int, []),
     "pdg_profile_stage_name": (C.c_char_p, [C.c_int]),
@@ -265,6 +269,14 @@ def pdg_eval(ctx, stream=None) -> np.ndarray:
     out = (C.c_double * 4)()
     _check(load().pdg_eval(ctx, out, _stream(stream)), ctx)
     return np.array(out[:], np.float64)
+
+
+def pdg_fit_mesh(ctx, p0, n_steps: int, lam: float = MESH_LAMBDA, lr: float = MESH_LR, stream=None) -> pdg_fit_stats:
+    """Template-mesh fit of the context's vertices to the keyframe cloud p0 [n, 3]."""
+    a = _Arr(p0, np.float32, 3, "p0")
+    st = pdg_fit_stats()
+    _check(load().pdg_fit_mesh(ctx, a.ptr, a.n, int(n_steps), float(lam), float(lr), C.byref(st), _stream(stream)), ctx)
+    return st
 
 
 def pdg_precondition(ctx, level: int, g, out, stream=None):

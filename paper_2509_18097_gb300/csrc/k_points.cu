@@ -35,7 +35,9 @@ __global__ void k_plan(Plan* P) {
     Job* J = P->jobs[j];
     const int G = 1 << J->mov.bits;
     cnt[ST_Q][j] = J->Q;
-    cnt[ST_NNQ][j] = J->Q + 2 * J->M;
+    // reverse queries into the source set only when there is one (a template-mesh fit has none)
+    const int nrs = J->N > 0 ? 2 : 1;
+    cnt[ST_NNQ][j] = J->Q + nrs * J->M;
     cnt[ST_E][j] = J->E;
     cnt[ST_MOVCH][j] = (2 * G * G * G + SCAN_CHUNK - 1) / SCAN_CHUNK;
     int a = 0, t = 0, p3 = 0, cols = 0, ad = 0;
@@ -77,7 +79,7 @@ __global__ void k_plan(Plan* P) {
     cnt[ST_COL][j] = cols;
     cnt[ST_ADAM][j] = ad;
     cnt[ST_JOB][j] = 1;
-    cnt[ST_LOSSCH][j] = (J->Q + 2 * J->M + J->E + LOSS_CHUNK - 1) / LOSS_CHUNK;
+    cnt[ST_LOSSCH][j] = (J->Q + nrs * J->M + J->E + LOSS_CHUNK - 1) / LOSS_CHUNK;
   }
   __syncthreads();
   if (threadIdx.x < NSTAGE) {
@@ -292,7 +294,7 @@ __global__ void k_assemble(const Plan* __restrict__ P) {
 // ------------------------------------------------------------------------------ loss
 
 // Loss record.  The per-query and per-edge terms of a job form one virtual array
-// [phi fwd (Q) | phi rev set 0 (M) | phi rev set 1 (M) | |r| (E)], cut into fixed chunks of
+// [phi fwd (Q) | phi rev set 0 (M) | phi rev set 1 (M, if N > 0) | |r| (E)], cut into fixed chunks of
 // LOSS_CHUNK; each chunk is summed by one block in a fixed fp32 tree per term, and a second
 // kernel adds a job's chunk partials in order in FP64.  The partition depends only on the
 // job, so a job's loss is bitwise the same alone or in a batch.
@@ -322,14 +324,15 @@ __global__ void __launch_bounds__(256) k_loss_chunks(const Plan* __restrict__ P)
     const int c = it - P->pre[ST_LOSSCH][j];
     const int b0 = c * LOSS_CHUNK;
     const int Q = J.Q, V = J.V, M = J.M;
-    const int n_all = Q + 2 * M + J.E;
+    const int rev_end = Q + (J.N > 0 ? 2 : 1) * M;
+    const int n_all = rev_end + J.E;
     float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
     for (int i = b0 + threadIdx.x; i < min(b0 + LOSS_CHUNK, n_all); i += blockDim.x) {
       if (i < V) s0 += J.loss_fwd[i];
       else if (i < Q) s1 += J.loss_fwd[i];
       else if (i < Q + M) s2 += J.loss_rev[i - Q];
-      else if (i < Q + 2 * M) s3 += J.loss_rev[i - Q];
-      else s4 += J.loss_iso[i - Q - 2 * M];
+      else if (i < rev_end) s3 += J.loss_rev[i - Q];
+      else s4 += J.loss_iso[i - rev_end];
     }
     const float t0 = block_sum(s0, red), t1 = block_sum(s1, red), t2 = block_sum(s2, red);
     const float t3 = block_sum(s3, red), t4 = block_sum(s4, red);
@@ -345,7 +348,7 @@ __global__ void __launch_bounds__(256) k_loss_final(const Plan* __restrict__ P) 
   const int nj = P->n_jobs;
   for (int j = blockIdx.x; j < nj; j += gridDim.x) {
     const Job& J = *P->jobs[j];
-    const int nch = (J.Q + 2 * J.M + J.E + LOSS_CHUNK - 1) / LOSS_CHUNK;
+    const int nch = (J.Q + (J.N > 0 ? 2 : 1) * J.M + J.E + LOSS_CHUNK - 1) / LOSS_CHUNK;
     float s[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     for (int c = threadIdx.x; c < nch; c += blockDim.x) {
 #pragma unroll
@@ -356,7 +359,7 @@ __global__ void __launch_bounds__(256) k_loss_final(const Plan* __restrict__ P) 
     for (int k = 0; k < 5; ++k) t[k] = (double)block_sum(s[k], red);  // all terms are >= 0
     if (threadIdx.x == 0) {
       const double cdm = t[0] / J.V + t[2] / J.M;
-      const double cdp = t[1] / (J.Q - J.V) + t[3] / J.M;
+      const double cdp = J.N > 0 ? t[1] / (J.Q - J.V) + t[3] / J.M : 0.0;
       const double iso = J.E > 0 ? t[4] / J.E : 0.0;
       const double tot = (double)J.w_mesh * cdm + (double)J.w_pts * cdp + (double)J.w_iso * iso;
       J.loss[0] = tot;

@@ -48,6 +48,13 @@ void launch_aos_to_soa(const float* in, float* out, int n3, cudaStream_t s, int 
 void launch_zmask(Job* J, const Job& hJ, cudaStream_t s);
 void launch_sobz_pivots(float* piv, int* slow, const float* mu, int n, float lam, cudaStream_t s);
 
+// template-mesh fit (k_mesh.cu)
+void launch_mesh_points(Job* J, int V, cudaStream_t s);
+void launch_mesh_solve(const int* v2e_ptr, const int* v2e, const int2* edges, const float4* b, float4* h, float4* r,
+                       float4* d0, float4* d1, int V, float lam, float emax, int iters, cudaStream_t s);
+void launch_mesh_adam(float4* x, const float4* g, float4* m, float4* v, int V, float lr, float b1, float b2, float eps,
+                      float bias1, float ibias2, cudaStream_t s);
+
 // misc conversions
 void launch_soa_to_aos(const float* in, float* out, int n3, cudaStream_t s, int C = 3);
 void launch_pack_theta(const float* in, float4* th, float4* tht, int n3, int C, cudaStream_t s);

@@ -86,6 +86,9 @@ struct pdg_ctx {
   Job* op_job = nullptr;   // scratch job / plan for single-level operations
   Plan* op_plan = nullptr;
   int* dflag = nullptr;
+  float4* mesh = nullptr;  // [7][V]: h, r, d0, d1, preconditioned gradient, Adam m, Adam v
+  int max_degree = 0;      // largest vertex degree of the mesh (bounds the Laplacian's spectrum)
+  bool mesh_valid = false; // a template-mesh fit has run (PDG_BUF_MESH_* readable)
   float* stage = nullptr;  // [stage_pts][3] staging of host inputs
   int stage_pts = 0;
   int nmax = 1;
@@ -143,6 +146,7 @@ struct Layout {
   size_t src4, tgt4, verts4;
   size_t t_hist, t_off, t_keys, t_pts, t_csum, m_hist, m_off, m_keys, m_pts, m_csum;
   size_t hard, hard_count, step, bias, loss, status, loss_part, gmax, counters;
+  size_t mesh;  // template-mesh fit: 7 float4 [V] arrays (gradient copy, solves, Adam moments)
   int tbits, mbits;
 };
 
@@ -236,6 +240,7 @@ Layout make_layout(const pdg_config& c, int V, int E, int max_pts) {
   L.status = a.take<int>(1);
   L.gmax = a.take<unsigned>(1);
   L.counters = a.take<unsigned long long>(4);
+  L.mesh = a.take<float4>(7 * (size_t)V);
   L.total = (a.off + 255) & ~size_t(255);
   return L;
 }
@@ -503,7 +508,10 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
     c->v2e_ptr[he[2 * e] + 1]++;
     c->v2e_ptr[he[2 * e + 1] + 1]++;
   }
-  for (int v = 0; v < n_verts; ++v) c->v2e_ptr[v + 1] += c->v2e_ptr[v];
+  for (int v = 0; v < n_verts; ++v) {
+    c->max_degree = std::max(c->max_degree, c->v2e_ptr[v + 1]);
+    c->v2e_ptr[v + 1] += c->v2e_ptr[v];
+  }
   c->v2e.assign(std::max(2 * n_edges, 1), 0);
   {
     std::vector<int> fill(c->v2e_ptr.begin(), c->v2e_ptr.end() - 1);
@@ -551,6 +559,7 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
   c->op_job = (Job*)P(L.op_job);
   c->op_plan = (Plan*)P(L.op_plan);
   c->dflag = (int*)P(L.flag);
+  c->mesh = (float4*)P(L.mesh);
   c->stage = (float*)P(L.stage);
   c->stage_pts = std::max(n_verts, max_pts);
   std::vector<float> mu;
@@ -747,6 +756,7 @@ pdg_status pdg_begin_frame(pdg_ctx* c, const float* target_xyz, int n_tgt, void*
   launch_csr_build(c->dJ, J, s);
   CU(c, cudaGetLastError());
   c->in_frame = true;
+  c->mesh_valid = false;  // the step overwrites the mesh fit's gradient
   c->steps_in_frame = 0;
   c->plan_stale = true;
   ++c->frame_gen;
@@ -921,6 +931,11 @@ pdg_status pdg_read(pdg_ctx* c, int which, int level, void* out, size_t out_byte
     case PDG_BUF_LOSS: need = 4 * sizeof(double); break;
     case PDG_BUF_SOURCE: need = sizeof(float) * 3 * (size_t)J.N; break;
     case PDG_BUF_COUNTERS: need = 4 * sizeof(unsigned long long); break;
+    case PDG_BUF_MESH_GRAD:
+    case PDG_BUF_MESH_PGRAD:
+      if (!c->mesh_valid) return c->fail(PDG_ERR_STATE, "no template-mesh fit has run");
+      need = sizeof(float) * 3 * (size_t)c->V;
+      break;
     default: return c->fail(PDG_ERR_INVALID, "unknown buffer");
   }
   if (out_bytes < need) return c->fail(PDG_ERR_INVALID, "output buffer too small");
@@ -942,6 +957,8 @@ pdg_status pdg_read(pdg_ctx* c, int which, int level, void* out, size_t out_byte
     case PDG_BUF_Y: launch_unpack4(J.y, tmp, J.Q, s); break;
     case PDG_BUF_POINT_GRAD: launch_unpack4(J.gy, tmp, J.Q, s); break;
     case PDG_BUF_SOURCE: launch_unpack4(J.src4, tmp, J.N, s); break;
+    case PDG_BUF_MESH_GRAD: launch_unpack4(J.gy, tmp, c->V, s); break;
+    case PDG_BUF_MESH_PGRAD: launch_unpack4(c->mesh + 4 * (size_t)c->V, tmp, c->V, s); break;
   }
   const pdg_status st = copy_out(c, out, tmp, need, s);
   cudaFreeAsync(tmp, s);
@@ -1021,6 +1038,98 @@ pdg_status pdg_precondition(pdg_ctx* c, int level, const float* g, float* out, v
   cudaFreeAsync(tmp, s);
   CU(c, cudaMemsetAsync(lv.g, 0, bytes, s));
   CU(c, cudaStreamSynchronize(s));
+  return st;
+}
+
+// ------------------------------------------------------------------------------ template-mesh fit
+
+pdg_status pdg_fit_mesh(pdg_ctx* c, const float* p0_xyz, int n_p0, int n_steps, float lambda, float lr,
+                        pdg_fit_stats* stats, void* cuda_stream) {
+  if (!c) return PDG_ERR_INVALID;
+  if (c->in_frame) return c->fail(PDG_ERR_STATE, "pdg_fit_mesh only between frames");
+  if (!p0_xyz || n_p0 < 1 || n_steps < 0 || !(lambda >= 0.f) || !(lambda < 1e30f) || !(lr >= 0.f) || !(lr < 1e30f))
+    return c->fail(PDG_ERR_INVALID, "bad mesh-fit arguments");
+  if (n_p0 > c->max_pts) return c->fail(PDG_ERR_BUDGET, "cloud larger than max_pts");
+  // bounds the Chebyshev iteration count below (about 5000 per solve at the limit)
+  if ((double)lambda * std::max(c->max_degree, 1) > 1e5)
+    return c->fail(PDG_ERR_INVALID, "lambda times the largest vertex degree above 1e5");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  Job& J = c->h;
+  const int V = c->V;
+  TRY(load_points(c, p0_xyz, n_p0, J.tgt4, s, true));
+  // the step's kernels on a job whose query points are the mesh vertices alone: no source set,
+  // no isometry, the mesh term with weight 1; 3 channels (the grids take no part)
+  Job mj = J;
+  mj.N = 0;
+  mj.Q = V;
+  mj.M = n_p0;
+  mj.E = 0;
+  mj.C = 3;
+  mj.w_mesh = 1.f;
+  mj.w_pts = 0.f;
+  mj.w_iso = 0.f;
+  mj.count_nn = 0;
+  CU(c, cudaMemcpyAsync(c->op_job, &mj, sizeof(Job), cudaMemcpyHostToDevice, s));
+  Plan op;
+  std::memset(&op, 0, sizeof(op));
+  op.n_jobs = 1;
+  op.jobs[0] = c->op_job;
+  CU(c, cudaMemcpyAsync(c->op_plan, &op, sizeof(Plan), cudaMemcpyHostToDevice, s));
+  launch_plan(c->op_plan, s);
+  float4* h = c->mesh;
+  float4* r = h + V;
+  float4* d0 = r + V;
+  float4* d1 = d0 + V;
+  float4* pg = d1 + V;
+  float4* am = pg + V;
+  float4* av = am + V;
+  CU(c, cudaMemcpyAsync(J.x, J.verts4, sizeof(float4) * V, cudaMemcpyDeviceToDevice, s));  // X_0 being fitted
+  CU(c, cudaMemsetAsync(am, 0, 2 * sizeof(float4) * (size_t)V, s));
+  CU(c, cudaMemsetAsync(J.nn_fwd, 0xff, sizeof(int) * (size_t)V, s));
+  CU(c, cudaMemsetAsync(J.nn_rev, 0xff, sizeof(int) * (size_t)n_p0, s));
+  CU(c, cudaMemsetAsync(J.loss, 0, 4 * sizeof(double), s));
+  CU(c, cudaMemsetAsync(J.status, 0, sizeof(int), s));
+  launch_tgt_build(c->op_job, mj, s);
+  // Chebyshev interval: the Laplacian's eigenvalues lie in [0, 2 max degree] (Gershgorin), so
+  // those of I + lambda L in [1, emax]; iterations for a relative error below 1e-7 in exact
+  // arithmetic, 2 sqrt(kappa) q^k <= 1e-7 with q = (sqrt(kappa) - 1) / (sqrt(kappa) + 1)
+  const double emax = 1.0 + 2.0 * lambda * std::max(c->max_degree, 1);
+  const double sk = std::sqrt(emax);
+  const double q = (sk - 1.0) / (sk + 1.0);
+  const int iters = q > 0.0 ? (int)std::ceil(std::log(1e-7 / (2.0 * sk)) / std::log(q)) : 1;
+  const int2* edges = J.edges;
+  for (int k = 1; k <= n_steps; ++k) {
+    launch_mesh_points(c->op_job, V, s);
+    for (int i = S_MOV_SCAN; i <= S_NN_HARD; ++i) launch_stage(i, c->op_plan, 1, c->sms, s);
+    launch_stage(S_ASSEMBLE, c->op_plan, 1, c->sms, s);
+    launch_stage(S_LOSS, c->op_plan, 1, c->sms, s);
+    // (I + lambda L)^{-2} dL/dX by two solves, then Adam on the vertices
+    launch_mesh_solve(J.v2e_ptr, J.v2e, edges, J.gy, h, r, d0, d1, V, lambda, (float)emax, iters, s);
+    launch_mesh_solve(J.v2e_ptr, J.v2e, edges, h, pg, r, d0, d1, V, lambda, (float)emax, iters, s);
+    const float bias1 = (float)(1.0 / (1.0 - std::pow((double)J.beta1, k)));
+    const float ibias2 = (float)(1.0 / std::sqrt(1.0 - std::pow((double)J.beta2, k)));
+    launch_mesh_adam(J.x, pg, am, av, V, lr, J.beta1, J.beta2, J.eps, bias1, ibias2, s);
+    CU(c, cudaGetLastError());
+  }
+  CU(c, cudaMemcpyAsync(J.verts4, J.x, sizeof(float4) * V, cudaMemcpyDeviceToDevice, s));
+  double loss[4];
+  int status = 0;
+  CU(c, cudaMemcpyAsync(loss, J.loss, sizeof(loss), cudaMemcpyDeviceToHost, s));
+  CU(c, cudaMemcpyAsync(&status, J.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CU(c, cudaStreamSynchronize(s));
+  c->mesh_valid = n_steps > 0;
+  c->plan_stale = true;  // the frame plan is recomputed at the next frame
+  const pdg_status st = status ? PDG_ERR_NONFINITE : PDG_OK;
+  if (stats) {
+    stats->loss_total = loss[0];
+    stats->cd_mesh = loss[1];
+    stats->cd_pts = 0.0;
+    stats->iso = 0.0;
+    stats->n_steps = n_steps;
+    stats->status = st;
+    stats->nn_ties = -1;
+  }
+  if (st != PDG_OK) c->err = "a loss became NaN or Inf during the mesh fit";
   return st;
 }
 
