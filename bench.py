@@ -381,6 +381,29 @@ def run_reference(args, world, rank):
 # ------------------------------------------------------------------------------ GPU arm
 
 
+def run_mesh_fit(B, ctx, state0, p0, stream, iters=50):
+    """Template-mesh fit (Sec. 3.4 L_mesh = CD_R(X_0, P_0); Sec. 3.6 lambda = 16, lr = 1e-4)
+    of the headline template to its 100k-point keyframe cloud, between frames: device time
+    per iteration (CUDA events around one call of `iters` iterations, after a warm call)."""
+    import torch
+
+    B.pdg_load_state(ctx, state0)
+    B.pdg_fit_mesh(ctx, p0, 3, stream=stream.cuda_stream)
+    B.pdg_load_state(ctx, state0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st = B.pdg_fit_mesh(ctx, p0, iters, stream=stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / iters
+    B.pdg_load_state(ctx, state0)
+    return {"iterations": iters, "ms_per_iteration": ms, "iterations_per_s": 1000.0 / ms,
+            "loss_last": st.cd_mesh, "lambda": B.MESH_LAMBDA, "lr": B.MESH_LR,
+            "note": "eager launches: the step's Chamfer kernels on the vertices, two Chebyshev solves "
+                    "of (I + lambda L) (135 one-kernel iterations each at max degree 6), Adam"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -569,6 +592,7 @@ def main():
            "d2h_bytes_per_step": (V * 12 + 48) / STEPS_PER_FRAME_E2E,
            "frame": f"pdg_fit_frame({STEPS_PER_FRAME_E2E} steps, host target) + pdg_get_vertices(host)",
            "final_loss": stats.loss_total}
+    mesh_fit = run_mesh_fit(B, ctx, state0, T(w.source), stream)
     B.pdg_destroy(ctx)
 
     serving = None
@@ -597,6 +621,7 @@ def main():
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
             "roofline": roof, "cpu_baseline": cpu, "stages": stages, "whole_step": whole_step,
             "resident_l2_steps_per_s": 1000.0 / resident_ms, "wall_s_timed": wall, "serving": serving,
+            "mesh_fit": mesh_fit,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
