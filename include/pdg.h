@@ -59,7 +59,8 @@ typedef enum pdg_status {
  * without preconditioning the learning rate is scaled by 0.1 (Sec. 4, ablation). */
 typedef struct pdg_config {
   int n_levels;               /* 1..PDG_MAX_LEVELS */
-  int res[PDG_MAX_LEVELS];    /* vertices per axis, coarse -> fine: 1 or a power of two <= 256 */
+  int res[PDG_MAX_LEVELS];    /* vertices per axis, coarse -> fine: 1, or 2^a 3^b in 2..256 (the
+                                 preconditioner's line transforms are radix-2/3 FFTs) */
   float lo[3], hi[3];         /* grid domain (default [-1.5, 1.5]^3); points outside are clamped */
   float alpha;                /* robust Chamfer weight exp(-alpha d^2) */
   float w_chamfer_mesh;       /* weight of CD_R(X_hat_t, P_t) (the confidence weight; 1) */
@@ -78,8 +79,8 @@ typedef struct pdg_config {
  * rotation part of Sec. 3.3 held at the identity).  CAYLEY: the 6-D vector T = (z, t) of
  * Sec. 3.3; the averaged T(x) (Eq. 1) moves x to R(z) x + t with R(z) = (I + Z)(I - Z)^{-1},
  * Z the skew-symmetric matrix of z (rotation about the world origin).  Level values are then
- * float [res^3][6] ordered (z0, z1, z2, t0, t1, t2), and every level must have at most 128
- * vertices per axis (PDG_ERR_INVALID otherwise). */
+ * float [res^3][6] ordered (z0, z1, z2, t0, t1, t2), and every level must have 1 or a power
+ * of two up to 128 vertices per axis (PDG_ERR_INVALID otherwise). */
 #define PDG_PAYLOAD_DISPLACEMENT 0
 #define PDG_PAYLOAD_CAYLEY 1
 

@@ -66,7 +66,7 @@ __global__ void k_plan(Plan* P) {
       lv.adj_lg = lg;
       if (lg == 6) a += na;
       else aw += (na + (32 >> lg) - 1) >> (5 - lg);
-      if (J->lev[l].n > 128) t += J->lev[l].tiles;
+      if (tile_level(J->lev[l].n)) t += J->lev[l].tiles;
       else {
         p3 += J->lev[l].n;
         cols += J->C * ((J->lev[l].n * J->lev[l].n + 63) / 64);  // blocks of 64 columns (two threads each)

@@ -1,6 +1,7 @@
 // Grid Sobolev preconditioning (Sec. 3.2, Eq. 3) fused with the Adam update (Sec. 3.6) for
-// levels of 256^3 vertices, whose planes do not fit in shared memory (smaller levels use
-// the three-pass plane path of k_sobolev_plane.cu).
+// levels of 256^3 vertices, whose planes do not fit in shared memory, and for levels whose
+// resolution has a factor 3 (2^a 3^b vertices per axis; powers of two up to 128 use the
+// three-pass plane path of k_sobolev_plane.cu).
 //
 // L_l is the 6-neighbour graph Laplacian of the level's vertex grid with a free
 // boundary; it is the Kronecker sum of three path-graph Laplacians whose eigenvectors are
@@ -13,23 +14,34 @@
 //   3: z-lines,      DCT-II, spectral scale (incl. 1/n^3), inverse -> tmp
 //   4: y-lines,      inverse
 //   5: x-lines,      inverse, then Adam on theta/m/v of those vertices.
-// A line transform of length n = 2^p is done two lines at a time by one warp: the lines
+// A line transform of length n = 2^a 3^b is done two lines at a time by one warp: the lines
 // are packed as the real and imaginary parts of one complex sequence (after the
-// even/odd reordering that turns a DCT-II into a DFT), transformed by a radix-2 Stockham
-// FFT in shared memory, and separated with the conjugate-symmetry of real spectra.
+// even/odd reordering that turns a DCT-II into a DFT, valid for odd n too), transformed by
+// a mixed radix-2/3 Stockham FFT in shared memory (a radix-2 stages, then b radix-3
+// stages), and separated with the conjugate-symmetry of real spectra.
 #include "kernels.h"
 
 namespace pdg {
 
 constexpr int TS = 33;  // padded tile stride (floats) between consecutive elements of a line
 
-int sobolev_smem_bytes(int n) { return 3 * n * TS * 4 + SOB_WARPS * 2 * n * 8; }
+// floats of the tile (3 channels x n elements x TS lines), rounded up to an even count so
+// that the float2 FFT scratch after it is 8-byte aligned for odd n too
+__host__ __device__ constexpr int tile_floats(int n) { return (3 * n * TS + 1) & ~1; }
 
+int sobolev_smem_bytes(int n) { return tile_floats(n) * 4 + SOB_WARPS * 2 * n * 8; }
+
+// Stockham autosort FFT of n = 2^a 3^b points, one warp, ping-ponging between src and dst;
+// returns the buffer holding the result (natural order).  Stage with radix R after Ns
+// points' worth of earlier radices: for j < n / R, k = j mod Ns, the R inputs
+// src[j + r n / R] times exp(-2 pi i r k / (Ns R)) go through an R-point DFT into
+// dst[(j - k) R + k + r Ns].  tw[m] = exp(-2 pi i m / n).
 template <bool INV>
 __device__ __forceinline__ float2* fft_warp(float2* src, float2* dst, const float2* __restrict__ tw, int n,
                                             int lane) {
   const int half = n >> 1;
-  for (int Ns = 1; Ns < n; Ns <<= 1) {
+  const int p2 = n & -n;  // 2^a
+  for (int Ns = 1; Ns < p2; Ns <<= 1) {
     const int step = half / Ns;
     for (int j = lane; j < half; j += 32) {
       const int k = j & (Ns - 1);
@@ -46,10 +58,40 @@ __device__ __forceinline__ float2* fft_warp(float2* src, float2* dst, const floa
     src = dst;
     dst = sw;
   }
+  // radix 3: y_0 = a + s, y_{1,2} = a - s / 2 -+ i (sqrt(3) / 2) (b - c), s = b + c (forward);
+  // the inverse conjugates the twiddles and the sign of the i term
+  const int third = n / 3;
+  const float h3 = INV ? -0.866025403784438647f : 0.866025403784438647f;
+  for (int Ns = p2; Ns < n; Ns *= 3) {
+    const int step = n / (3 * Ns);
+    for (int j = lane; j < third; j += 32) {
+      const int k = j % Ns;
+      float2 w1 = __ldg(tw + k * step), w2 = __ldg(tw + 2 * k * step);
+      if (INV) {
+        w1.y = -w1.y;
+        w2.y = -w2.y;
+      }
+      const float2 a = src[j], b0 = src[j + third], c0 = src[j + 2 * third];
+      const float2 b = make_float2(b0.x * w1.x - b0.y * w1.y, b0.x * w1.y + b0.y * w1.x);
+      const float2 c = make_float2(c0.x * w2.x - c0.y * w2.y, c0.x * w2.y + c0.y * w2.x);
+      const float2 sm = make_float2(b.x + c.x, b.y + c.y), df = make_float2(b.x - c.x, b.y - c.y);
+      const float2 m = make_float2(a.x - 0.5f * sm.x, a.y - 0.5f * sm.y);
+      const int d = (j - k) * 3 + k;
+      dst[d] = make_float2(a.x + sm.x, a.y + sm.y);
+      dst[d + Ns] = make_float2(m.x + h3 * df.y, m.y - h3 * df.x);
+      dst[d + 2 * Ns] = make_float2(m.x - h3 * df.y, m.y + h3 * df.x);
+    }
+    __syncwarp();
+    float2* sw = src;
+    src = dst;
+    dst = sw;
+  }
   return src;
 }
 
-__device__ __forceinline__ int dct_src(int j, int n) { return j < (n >> 1) ? 2 * j : 2 * (n - 1 - j) + 1; }
+// even/odd reordering of a DCT-II input (any n): v[j] = x[2j] for j < ceil(n / 2), then
+// the odd elements in reverse
+__device__ __forceinline__ int dct_src(int j, int n) { return j < ((n + 1) >> 1) ? 2 * j : 2 * (n - 1 - j) + 1; }
 
 // A, B <- C A, C B (unnormalised DCT-II), lines with element stride TS
 __device__ void dct2_pair(float* A, float* B, int n, float2* b0, float2* b1, const float2* __restrict__ tw,
@@ -62,7 +104,7 @@ __device__ void dct2_pair(float* A, float* B, int n, float2* b0, float2* b1, con
   const float2* Z = fft_warp<false>(b0, b1, tw, n, lane);
   for (int k = lane; k < n; k += 32) {
     const float2 zk = Z[k];
-    const float2 zc = Z[(n - k) & (n - 1)];
+    const float2 zc = Z[k ? n - k : 0];
     // V_A = (Z_k + conj Z_{n-k}) / 2,  V_B = (Z_k - conj Z_{n-k}) / (2i)
     const float2 va = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y - zc.y));
     const float2 vb = make_float2(0.5f * (zk.y + zc.y), -0.5f * (zk.x - zc.x));
@@ -97,13 +139,26 @@ __device__ void dct3_pair(float* A, float* B, int n, float2* b0, float2* b1, con
 }
 
 // flat vertex index of element e of line r of a level (axis 0: x-lines, r = z n + y;
-// axis 1: y-lines, r = z n + x; axis 2: z-lines, r = y n + x)
+// axis 1: y-lines, r = z n + x; axis 2: z-lines, r = y n + x); lg = log2(n), or -1 when n
+// is not a power of two
 template <int AXIS>
 __device__ __forceinline__ int eaddr(int n, int lg, int r, int e) {
-  if (AXIS == 0) return (r << lg) + e;
-  const int lo = r & (n - 1), hi = r >> lg;
-  if (AXIS == 1) return (((hi << lg) + e) << lg) + lo;
-  return (((e << lg) + hi) << lg) + lo;
+  if (lg >= 0) {
+    if (AXIS == 0) return (r << lg) + e;
+    const int lo = r & (n - 1), hi = r >> lg;
+    if (AXIS == 1) return (((hi << lg) + e) << lg) + lo;
+    return (((e << lg) + hi) << lg) + lo;
+  }
+  if (AXIS == 0) return r * n + e;
+  const int hi = r / n, lo = r - hi * n;
+  if (AXIS == 1) return (hi * n + e) * n + lo;
+  return (e * n + hi) * n + lo;
+}
+
+// (quotient, remainder) of i by n, by shifts when n = 2^lg
+__device__ __forceinline__ void divmod_n(int i, int n, int lg, int& q, int& rm) {
+  q = lg >= 0 ? i >> lg : i / n;
+  rm = i - q * n;
 }
 
 template <int PASS>
@@ -121,7 +176,7 @@ __global__ void __launch_bounds__(SOB_THREADS) k_sob(const Plan* __restrict__ P)
     int t = it - P->pre[ST_TILE][j];
     int l = 0;
     for (; l < J.L; ++l) {
-      if (J.lev[l].n <= 128) continue;
+      if (!tile_level(J.lev[l].n)) continue;
       if (t < J.lev[l].tiles) break;
       t -= J.lev[l].tiles;
     }
@@ -130,7 +185,7 @@ __global__ void __launch_bounds__(SOB_THREADS) k_sob(const Plan* __restrict__ P)
     const int n = lv.n, lg = lv.lg, n3 = lv.n3, nl = n * n;
     const int r0 = t * TILE_LINES;
     float* tl = smem;
-    float2* b0 = reinterpret_cast<float2*>(smem + 3 * n * TS) + warp * 2 * n;
+    float2* b0 = reinterpret_cast<float2*>(smem + tile_floats(n)) + warp * 2 * n;
     float2* b1 = b0 + n;
     const float* src = (PASS == 1 || (PASS == 5 && !pre)) ? lv.g : lv.tmp;
 
@@ -138,7 +193,7 @@ __global__ void __launch_bounds__(SOB_THREADS) k_sob(const Plan* __restrict__ P)
       const int c = idx / (TILE_LINES * n);
       const int rem = idx - c * TILE_LINES * n;
       int tt, e;
-      if (AXIS == 0) { tt = rem >> lg; e = rem & (n - 1); }
+      if (AXIS == 0) divmod_n(rem, n, lg, tt, e);
       else { e = rem >> 5; tt = rem & 31; }
       const int r = r0 + tt;
       tl[(c * n + e) * TS + tt] = r < nl ? src[(size_t)c * n3 + eaddr<AXIS>(n, lg, r, e)] : 0.f;
@@ -155,8 +210,12 @@ __global__ void __launch_bounds__(SOB_THREADS) k_sob(const Plan* __restrict__ P)
           // spectral scale (1 + lambda (mu_kx + mu_ky + mu_kz))^{-2} / n^3; lines are
           // z-lines r = ky n + kx
           const int ra = r0 + tt, rb = ra + 1;
-          const float ma = __ldg(lv.mu + (ra & (n - 1))) + __ldg(lv.mu + ((ra >> lg) & (n - 1)));
-          const float mb = __ldg(lv.mu + (rb & (n - 1))) + __ldg(lv.mu + ((rb >> lg) & (n - 1)));
+          // (lines past n^2 in the last tile are padding: their indices are wrapped into range)
+          int qa, xa, qb, xb;
+          divmod_n(ra, n, lg, qa, xa);
+          divmod_n(rb, n, lg, qb, xb);
+          const float ma = __ldg(lv.mu + xa) + __ldg(lv.mu + qa % n);
+          const float mb = __ldg(lv.mu + xb) + __ldg(lv.mu + qb % n);
           const float inv_n3 = 1.f / (float)n3;
           for (int e = lane; e < n; e += 32) {
             const float me = __ldg(lv.mu + e);
@@ -177,7 +236,7 @@ __global__ void __launch_bounds__(SOB_THREADS) k_sob(const Plan* __restrict__ P)
         const int c = idx / (TILE_LINES * n);
         const int rem = idx - c * TILE_LINES * n;
         int tt, e;
-        if (AXIS == 0) { tt = rem >> lg; e = rem & (n - 1); }
+        if (AXIS == 0) divmod_n(rem, n, lg, tt, e);
         else { e = rem >> 5; tt = rem & 31; }
         const int r = r0 + tt;
         if (r < nl) lv.tmp[(size_t)c * n3 + eaddr<AXIS>(n, lg, r, e)] = tl[(c * n + e) * TS + tt];
@@ -188,10 +247,11 @@ __global__ void __launch_bounds__(SOB_THREADS) k_sob(const Plan* __restrict__ P)
       const float step = lv.lr * J.bias[0];
       const float ib2 = J.bias[1];
       for (int idx = threadIdx.x; idx < TILE_LINES * n; idx += SOB_THREADS) {
-        const int tt = idx >> lg, x = idx & (n - 1);
+        int tt, x;
+        divmod_n(idx, n, lg, tt, x);
         const int r = r0 + tt;
         if (r >= nl) continue;
-        const int v = (r << lg) + x;
+        const int v = r * n + x;
         float4 th = lv.theta[v];
         float* thc = &th.x;
 #pragma unroll

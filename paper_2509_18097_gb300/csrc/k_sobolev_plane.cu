@@ -256,11 +256,11 @@ __device__ __forceinline__ void dct3_pre(const float2 (&X)[N2], int t, int lbase
 }
 
 // maps a plane item of a job to (level, index); C n items per level (plane major, then
-// channel), only levels with n <= 128 take part
+// channel), only the plane-path levels (powers of two up to 128) take part
 __device__ __forceinline__ bool plane_item(const Job& J, int r, int& l, int& idx) {
   for (l = 0; l < J.L; ++l) {
     const int n = J.lev[l].n;
-    if (n > 128) continue;
+    if (tile_level(n)) continue;
     if (r < J.C * n) {
       idx = r;
       return true;
@@ -464,7 +464,7 @@ __device__ __forceinline__ void column_solve(float* __restrict__ t, const float*
 __device__ __forceinline__ bool column_item(const Job& J, int r, int& l, int& c, int& col0) {
   for (l = 0; l < J.L; ++l) {
     const int n = J.lev[l].n;
-    if (n > 128) continue;
+    if (tile_level(n)) continue;
     const int per = (n * n + COLS_PER_ITEM - 1) / COLS_PER_ITEM;
     if (r < J.C * per) {
       c = r / per;
@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(PL_THREADS, 2) k_sobp_inv(const Plan* __restri
 __device__ __forceinline__ bool adam_item(const Job& J, int r, int& l, int& q) {
   for (l = 0; l < J.L; ++l) {
     const int n = J.lev[l].n;
-    if (n > 128) continue;
+    if (tile_level(n)) continue;
     const int cnt = (J.lev[l].n3 + 3) >> 2;
     if (r < cnt) {
       q = r;

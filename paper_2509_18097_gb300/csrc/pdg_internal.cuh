@@ -136,6 +136,11 @@ struct Plan {
 
 // ------------------------------------------------------------------------------ helpers
 
+// Which preconditioner path takes a level of n vertices per axis: powers of two up to 128
+// (and n = 1) take the shared-memory plane path, 256 and the sizes with a factor 3 the
+// tile path with mixed radix-2/3 line transforms.
+__host__ __device__ __forceinline__ bool tile_level(int n) { return n > 128 || (n & (n - 1)) != 0; }
+
 __device__ __forceinline__ int find_job(const int* pre, int n_jobs, int item) {
   int lo = 0, hi = n_jobs;
   while (hi - lo > 1) {

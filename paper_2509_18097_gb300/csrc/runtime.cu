@@ -36,7 +36,13 @@ int grid_bits(long count, double per_cell = 8.0) {
   return std::min(std::max(b, 2), 7);
 }
 
-bool valid_res(int n) { return n == 1 || (n >= 2 && n <= 256 && (n & (n - 1)) == 0); }
+// 1, or 2..256 with no prime factor but 2 and 3 (the line transforms are radix-2/3 FFTs)
+bool valid_res(int n) {
+  if (n < 1 || n > 256) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
 
 int ilog2(int n) {
   int l = 0;
@@ -92,6 +98,7 @@ struct pdg_ctx {
   float* stage = nullptr;  // [stage_pts][3] staging of host inputs
   int stage_pts = 0;
   int nmax = 1;
+  int ntile = 0;  // largest resolution among the levels the tile path preconditions (0: none)
   cudaStream_t cap = nullptr, cap2 = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int graph_kernels = 0;   // kernel nodes of gexec
@@ -120,6 +127,7 @@ struct pdg_batch {
   cudaStream_t cap = nullptr, cap2 = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int graph_nmax = 0;
+  int graph_ntile = 0;
   bool dirty = true;  // membership changed since the last upload of the job table
   std::string err;
 };
@@ -173,7 +181,7 @@ Layout make_layout(const pdg_config& c, int V, int E, int max_pts) {
     v.g = a.take<float>(C * n3);
     v.tmp = a.take<float>(C * n3);
     v.zmask = a.take<int>(n);
-    v.piv = a.take<float>(n <= 128 ? (n / 2 + 1) * n * n : 1);
+    v.piv = a.take<float>(tile_level(n) ? 1 : (n / 2 + 1) * n * n);
     v.piv_slow = a.take<int>(1);
     v.mu = a.take<float>(n);
     v.tw = a.take<float2>(n);
@@ -249,11 +257,12 @@ const char* check_config(const pdg_config* c) {
   if (!c) return "config is NULL";
   if (c->n_levels < 1 || c->n_levels > PDG_MAX_LEVELS) return "n_levels must be in 1..8";
   for (int l = 0; l < c->n_levels; ++l)
-    if (!valid_res(c->res[l])) return "each res must be 1 or a power of two in 2..256";
+    if (!valid_res(c->res[l])) return "each res must be 1 or 2^a 3^b in 2..256";
   if (c->payload != PDG_PAYLOAD_DISPLACEMENT && c->payload != PDG_PAYLOAD_CAYLEY) return "unknown payload";
   if (c->payload == PDG_PAYLOAD_CAYLEY)
     for (int l = 0; l < c->n_levels; ++l)
-      if (c->res[l] > 128) return "the Cayley payload takes levels of at most 128 vertices per axis";
+      if (tile_level(c->res[l]))
+        return "the Cayley payload takes levels of 1 or a power of two up to 128 vertices per axis";
   for (int a = 0; a < 3; ++a)
     if (!(std::isfinite(c->lo[a]) && std::isfinite(c->hi[a]) && c->hi[a] > c->lo[a])) return "domain must have lo < hi";
   const float f[] = {c->alpha, c->w_chamfer_mesh, c->w_chamfer_pts, c->w_iso, c->lr0, c->lr_growth, c->lambda0,
@@ -309,9 +318,12 @@ enum StageIndex {
 // Stage i of a step; bump: the job_bump mode of the interpolation stage (1: optimisation
 // step, 2: evaluation); count: the nearest-neighbour instances that count candidates and
 // exact ties.  The plan's item prefixes must be current (refresh_plan).
-void launch_stage(int i, const Plan* plan, int nmax, int sms, cudaStream_t s, int bump = 1, bool count = false) {
+// nmax: the largest level resolution; ntile: the largest one of the levels the tile path
+// preconditions (0: none)
+void launch_stage(int i, const Plan* plan, int nmax, int ntile, int sms, cudaStream_t s, int bump = 1,
+                  bool count = false) {
   const int grid = sms * 8;
-  const int smem = sobolev_smem_bytes(nmax);
+  const int smem = sobolev_smem_bytes(std::max(ntile, 2));
   const int tiles_per_sm = std::max(1, std::min(4, (227 * 1024) / std::max(smem, 1)));
   switch (i) {
     case S_INTERP: launch_interp(plan, grid, s, bump); break;
@@ -332,7 +344,7 @@ void launch_stage(int i, const Plan* plan, int nmax, int sms, cudaStream_t s, in
       break;
     }
     case S_SOB_256:
-      if (nmax > 128) launch_sobolev_tiles(plan, sms * tiles_per_sm, nmax, s);
+      if (ntile > 0) launch_sobolev_tiles(plan, sms * tiles_per_sm, ntile, s);
       break;
     case S_LOSS: launch_loss(plan, sms * 2, s); break;
   }
@@ -342,7 +354,7 @@ constexpr int ST_SOB_FIRST = S_SOB_XY_FWD, ST_SOB_LAST = S_SOB_256;  // precondi
 // Captures one step.  Two branches: the isometry kernel runs beside the moving grid's sort
 // and the nearest-neighbour passes (it needs only the deformed points), the loss reduction
 // beside the adjoint and the preconditioner (nothing downstream reads it).
-pdg_status capture_step(pdg_ctx* c, const Plan* plan, int nmax, cudaStream_t cap, cudaStream_t cap2,
+pdg_status capture_step(pdg_ctx* c, const Plan* plan, int nmax, int ntile, cudaStream_t cap, cudaStream_t cap2,
                         cudaGraphExec_t* out, std::string* err, int sms, int* n_kernels = nullptr) {
   cudaGraph_t g = nullptr;
   cudaEvent_t ev[4] = {};
@@ -358,22 +370,22 @@ pdg_status capture_step(pdg_ctx* c, const Plan* plan, int nmax, cudaStream_t cap
     return PDG_ERR_CUDA;
   }
   const bool count = c && c->h.count_nn;  // a batch graph never counts
-  launch_stage(S_INTERP, plan, nmax, sms, cap);  // starts the step of every job
+  launch_stage(S_INTERP, plan, nmax, ntile, sms, cap);  // starts the step of every job
   cudaEventRecord(ev[0], cap);
   cudaStreamWaitEvent(cap2, ev[0], 0);
-  launch_stage(S_ISO, plan, nmax, sms, cap2);
+  launch_stage(S_ISO, plan, nmax, ntile, sms, cap2);
   cudaEventRecord(ev[1], cap2);
-  launch_stage(S_MOV_SCAN, plan, nmax, sms, cap);
-  launch_stage(S_MOV_SCATTER, plan, nmax, sms, cap);
-  launch_stage(S_NN, plan, nmax, sms, cap, 1, count);
-  launch_stage(S_NN_HARD, plan, nmax, sms, cap, 1, count);
+  launch_stage(S_MOV_SCAN, plan, nmax, ntile, sms, cap);
+  launch_stage(S_MOV_SCATTER, plan, nmax, ntile, sms, cap);
+  launch_stage(S_NN, plan, nmax, ntile, sms, cap, 1, count);
+  launch_stage(S_NN_HARD, plan, nmax, ntile, sms, cap, 1, count);
   cudaStreamWaitEvent(cap, ev[1], 0);
-  launch_stage(S_ASSEMBLE, plan, nmax, sms, cap);
+  launch_stage(S_ASSEMBLE, plan, nmax, ntile, sms, cap);
   cudaEventRecord(ev[2], cap);
   cudaStreamWaitEvent(cap2, ev[2], 0);
-  launch_stage(S_LOSS, plan, nmax, sms, cap2);
+  launch_stage(S_LOSS, plan, nmax, ntile, sms, cap2);
   cudaEventRecord(ev[3], cap2);
-  for (int i = S_ADJOINT; i <= S_SOB_256; ++i) launch_stage(i, plan, nmax, sms, cap);  // adjoint, preconditioner, Adam
+  for (int i = S_ADJOINT; i <= S_SOB_256; ++i) launch_stage(i, plan, nmax, ntile, sms, cap);  // adjoint, preconditioner, Adam
   cudaStreamWaitEvent(cap, ev[3], 0);
   e = cudaStreamEndCapture(cap, &g);
   for (auto& x : ev) cudaEventDestroy(x);
@@ -569,7 +581,7 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
     const auto& o = L.lv[l];
     const int n = cfg->res[l];
     lv.n = n;
-    lv.lg = ilog2(n);
+    lv.lg = (n & (n - 1)) == 0 ? ilog2(n) : -1;
     lv.n3 = n * n * n;
     lv.tiles = (n * n + TILE_LINES - 1) / TILE_LINES;
     lv.lr = (float)(cfg->lr0 * std::pow((double)cfg->lr_growth, l) * (cfg->precondition ? 1.0 : 0.1));
@@ -604,6 +616,7 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
     lv.n_active = (int*)P(o.n_active);
     lv.csum = (int*)P(o.csum);
     c->nmax = std::max(c->nmax, n);
+    if (tile_level(n)) c->ntile = std::max(c->ntile, n);
     mu.resize(n);
     tw.resize(n);
     tw4.resize(n);
@@ -619,7 +632,7 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
         cudaMemcpyAsync(lv.tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(lv.tw4, tw4.data(), n * sizeof(float2), cudaMemcpyHostToDevice, s) != cudaSuccess)
       return bail(PDG_ERR_CUDA);
-    launch_sobz_pivots(lv.piv, lv.piv_slow, lv.mu, n, lv.lam, s);
+    if (!tile_level(n)) launch_sobz_pivots(lv.piv, lv.piv_slow, lv.mu, n, lv.lam, s);
   }
   J.x = (float4*)P(L.x);
   J.y = (float4*)P(L.y);
@@ -771,7 +784,7 @@ pdg_status pdg_step(pdg_ctx* c, int n_steps, void* cuda_stream) {
   if (!c->gexec) {
     // the captured launches must not start before this stream's pending set-up
     CU(c, cudaStreamSynchronize(s));
-    TRY(capture_step(c, c->dplan, c->nmax, c->cap, c->cap2, &c->gexec, &c->err, c->sms, &c->graph_kernels));
+    TRY(capture_step(c, c->dplan, c->nmax, c->ntile, c->cap, c->cap2, &c->gexec, &c->err, c->sms, &c->graph_kernels));
   }
   TRY(refresh_plan(c, s));
   for (int i = 0; i < n_steps; ++i) CU(c, cudaGraphLaunch(c->gexec, s));
@@ -800,7 +813,7 @@ pdg_status pdg_profile_step(pdg_ctx* c, int n_steps, double* stage_ms, void* cud
   for (int k = 0; k < n_steps && st == PDG_OK; ++k) {
     for (int i = 0; i < N_STAGES; ++i) {
       cudaEventRecord(ev[i], s);
-      launch_stage(i, c->dplan, c->nmax, c->sms, s, 1, c->h.count_nn != 0);
+      launch_stage(i, c->dplan, c->nmax, c->ntile, c->sms, s, 1, c->h.count_nn != 0);
     }
     cudaEventRecord(ev[N_STAGES], s);
     st = c->cuda(cudaEventSynchronize(ev[N_STAGES]), "profile step");
@@ -995,7 +1008,7 @@ pdg_status pdg_eval(pdg_ctx* c, double* loss, void* cuda_stream) {
   cudaStream_t s = (cudaStream_t)cuda_stream;
   TRY(refresh_plan(c, s));
   for (int i = 0; i < N_STAGES; ++i)  // no preconditioner, no Adam, no step count
-    if (i < ST_SOB_FIRST || i > ST_SOB_LAST) launch_stage(i, c->dplan, c->nmax, c->sms, s, 2, c->h.count_nn != 0);
+    if (i < ST_SOB_FIRST || i > ST_SOB_LAST) launch_stage(i, c->dplan, c->nmax, c->ntile, c->sms, s, 2, c->h.count_nn != 0);
   CU(c, cudaGetLastError());
   if (loss) {
     CU(c, cudaMemcpyAsync(loss, c->h.loss, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1031,7 +1044,7 @@ pdg_status pdg_precondition(pdg_ctx* c, int level, const float* g, float* out, v
   CU(c, cudaMemcpyAsync(c->op_job, &oj, sizeof(Job), cudaMemcpyHostToDevice, s));
   CU(c, cudaMemcpyAsync(c->op_plan, &op, sizeof(Plan), cudaMemcpyHostToDevice, s));
   launch_plan(c->op_plan, s);
-  for (int i = ST_SOB_FIRST; i <= ST_SOB_LAST; ++i) launch_stage(i, c->op_plan, lv.n, c->sms, s);
+  for (int i = ST_SOB_FIRST; i <= ST_SOB_LAST; ++i) launch_stage(i, c->op_plan, lv.n, tile_level(lv.n) ? lv.n : 0, c->sms, s);
   launch_soa_to_aos(lv.tmp, tmp, lv.n3, s);
   CU(c, cudaGetLastError());
   const pdg_status st = copy_out(c, out, tmp, bytes, s);
@@ -1100,9 +1113,9 @@ pdg_status pdg_fit_mesh(pdg_ctx* c, const float* p0_xyz, int n_p0, int n_steps, 
   const int2* edges = J.edges;
   for (int k = 1; k <= n_steps; ++k) {
     launch_mesh_points(c->op_job, V, s);
-    for (int i = S_MOV_SCAN; i <= S_NN_HARD; ++i) launch_stage(i, c->op_plan, 1, c->sms, s);
-    launch_stage(S_ASSEMBLE, c->op_plan, 1, c->sms, s);
-    launch_stage(S_LOSS, c->op_plan, 1, c->sms, s);
+    for (int i = S_MOV_SCAN; i <= S_NN_HARD; ++i) launch_stage(i, c->op_plan, 1, 0, c->sms, s);
+    launch_stage(S_ASSEMBLE, c->op_plan, 1, 0, c->sms, s);
+    launch_stage(S_LOSS, c->op_plan, 1, 0, c->sms, s);
     // (I + lambda L)^{-2} dL/dX by two solves, then Adam on the vertices
     launch_mesh_solve(J.v2e_ptr, J.v2e, edges, J.gy, h, r, d0, d1, V, lambda, (float)emax, iters, s);
     launch_mesh_solve(J.v2e_ptr, J.v2e, edges, h, pg, r, d0, d1, V, lambda, (float)emax, iters, s);
@@ -1184,13 +1197,14 @@ pdg_status pdg_batch_step(pdg_batch* b, int n_steps, void* cuda_stream) {
   if (!b || n_steps < 0) return PDG_ERR_INVALID;
   if (b->n == 0 || n_steps == 0) return PDG_OK;
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  int nmax = 1, sms = 1;
+  int nmax = 1, ntile = 0, sms = 1;
   for (auto* c : b->members) {
     if (!c->in_frame) {
       b->err = "batch member outside a frame";
       return PDG_ERR_STATE;
     }
     nmax = std::max(nmax, c->nmax);
+    ntile = std::max(ntile, c->ntile);
     sms = c->sms;
   }
   if (b->dirty) {
@@ -1214,13 +1228,14 @@ pdg_status pdg_batch_step(pdg_batch* b, int n_steps, void* cuda_stream) {
     b->gens.resize(b->members.size());
     for (size_t i = 0; i < b->members.size(); ++i) b->gens[i] = b->members[i]->frame_gen;
   }
-  if (!b->gexec || nmax > b->graph_nmax) {
+  if (!b->gexec || nmax > b->graph_nmax || ntile > b->graph_ntile) {
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;
     if (cudaStreamSynchronize(s) != cudaSuccess) return PDG_ERR_CUDA;
-    const pdg_status st = capture_step(nullptr, b->dplan, nmax, b->cap, b->cap2, &b->gexec, &b->err, sms);
+    const pdg_status st = capture_step(nullptr, b->dplan, std::max(nmax, b->graph_nmax), std::max(ntile, b->graph_ntile), b->cap, b->cap2, &b->gexec, &b->err, sms);
     if (st != PDG_OK) return st;
-    b->graph_nmax = nmax;
+    b->graph_nmax = std::max(nmax, b->graph_nmax);
+    b->graph_ntile = std::max(ntile, b->graph_ntile);
   }
   for (int i = 0; i < n_steps; ++i)
     if (cudaGraphLaunch(b->gexec, s) != cudaSuccess) return PDG_ERR_CUDA;

@@ -273,24 +273,30 @@ def torus_sequence(n_frames: int = 100, n_pts: int = 20_000, seed: int = 0):
     return v, e, (lambda k: torus_sequence_frame(k, n_frames, n_pts, seed))
 
 
-def smooth_pow2(n: float) -> int:
-    """Nearest power of two to n (grid sizes with a radix-2 transform)."""
-    return int(2 ** round(math.log2(max(n, 2))))
+# grid sizes the preconditioner's radix-2/3 line transforms take: 2^a 3^b in 2..256
+SMOOTH_SIZES = sorted({2**a * 3**b for a in range(9) for b in range(6) if 2 <= 2**a * 3**b <= 256})
+
+
+def smooth23(n: float) -> int:
+    """The size 2^a 3^b in 2..256 nearest to n on a log scale (ties to the smaller)."""
+    ln = math.log(max(n, 2.0))
+    return min(SMOOTH_SIZES, key=lambda m: (abs(math.log(m) - ln), m))
 
 
 def batched_job(i: int, scale: float = 1.0, n_pts: int | None = None):
     """Job i of the batched / served workload: shape in {sphere, torus, ellipsoid},
     points per frame log-uniform in [5k, 200k] (times `scale`; `n_pts` overrides the draw,
     e.g. for the 500k-point frames of the served trace), 3-5 levels with the finest
-    log-uniform in [32, 256] vertices per axis (rounded to a power of two), and an
+    log-uniform in [32, 256] vertices per axis (rounded to the nearest 2^a 3^b, each coarser
+    level half the next one, rounded the same way, at least 4), and an
     analytic deformation in {twist, bend, sinusoid}.  Returns a dict of arrays/params."""
     rng = np.random.Generator(np.random.PCG64(1000 + i))
     shape = ["sphere", "torus", "ellipsoid"][rng.integers(3)]
     drawn = int(math.exp(rng.uniform(math.log(5e3), math.log(2e5))) * scale)
     n_pts = max(drawn if n_pts is None else int(n_pts), 256)
     L = int(rng.integers(3, 6))
-    finest = smooth_pow2(math.exp(rng.uniform(math.log(32), math.log(256))))
-    res = tuple(max(4, smooth_pow2(finest / 2 ** (L - 1 - l))) for l in range(L))
+    finest = smooth23(math.exp(rng.uniform(math.log(32), math.log(256))))
+    res = tuple(max(4, smooth23(finest / 2 ** (L - 1 - l))) for l in range(L))
     kind = ["twist", "bend", "sinusoid"][rng.integers(3)]
     amp = rng.uniform(0.05, 0.1)
     fr = rng.uniform(1.0, 3.0)

@@ -68,8 +68,14 @@ def test_query_bytes(lib):
     verts = 16**3 + 32**3 + 64**3 + 128**3
     assert b > verts * 64
     assert b < 2 * 1024**3
-    bad = binding.pdg_config_default(res=(16, 48))  # 48 is not a power of two
-    assert binding.pdg_query_bytes(bad, 10, 10, 10) == 0
+    # resolutions: 1 or 2^a 3^b up to 256 (the line transforms are radix-2/3 FFTs)
+    for res in ((16, 48), (3, 9, 27, 81), (24, 96, 192), (1, 2, 256), (6, 18, 54, 162, 216, 243)):
+        assert binding.pdg_query_bytes(binding.pdg_config_default(res=res), 10, 10, 10) > 0, res
+    for res in ((16, 40), (5,), (7, 14), (256, 288), (0,), (512,)):
+        assert binding.pdg_query_bytes(binding.pdg_config_default(res=res), 10, 10, 10) == 0, res
+    # the Cayley payload takes plane-path levels only (1 or a power of two up to 128)
+    assert binding.pdg_query_bytes(binding.pdg_config_default(res=(16, 48), payload="cayley"), 10, 10, 10) == 0
+    assert binding.pdg_query_bytes(binding.pdg_config_default(res=(16, 128), payload="cayley"), 10, 10, 10) > 0
     assert binding.pdg_query_bytes(cfg, 0, 10, 10) == 0
 
 

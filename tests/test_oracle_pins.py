@@ -341,7 +341,8 @@ def test_laplacian_cosine_eigenmode(k):
     np.testing.assert_allclose(O.grid_laplacian(c), mode_eigenvalue(n, k) * c, atol=1e-12)
 
 
-@pytest.mark.parametrize("n,k,lam", [(8, (1, 0, 0), 0.25), (12, (3, 5, 2), 0.84375), (16, (15, 1, 9), 2.0)])
+@pytest.mark.parametrize("n,k,lam", [(8, (1, 0, 0), 0.25), (12, (3, 5, 2), 0.84375), (16, (15, 1, 9), 2.0),
+                                     (9, (8, 4, 1), 1.25), (18, (17, 2, 9), 1.1)])
 def test_sobolev_scales_cosine_mode_by_closed_form(n, k, lam):
     c = cosine_mode(n, k)
     g = np.stack([c, 2 * c, -c], -1)
@@ -350,7 +351,8 @@ def test_sobolev_scales_cosine_mode_by_closed_form(n, k, lam):
     np.testing.assert_allclose(out, f * g, atol=1e-12)
 
 
-@pytest.mark.parametrize("n,k,lam", [(8, (1, 0, 0), 0.25), (12, (3, 5, 2), 0.84375), (16, (15, 1, 9), 2.0)])
+@pytest.mark.parametrize("n,k,lam", [(8, (1, 0, 0), 0.25), (12, (3, 5, 2), 0.84375), (16, (15, 1, 9), 2.0),
+                                     (27, (26, 13, 0), 0.5), (48, (47, 3, 20), 2.8), (81, (40, 80, 1), 1.5)])
 def test_sobolev_spectral_scales_cosine_mode_by_closed_form(n, k, lam):
     c = cosine_mode(n, k)
     g = np.stack([c, 2 * c, -c], -1)
