@@ -25,9 +25,9 @@ namespace pdg {
 
 constexpr int TS = 33;  // padded tile stride (floats) between consecutive elements of a line
 
-// floats of the tile (3 channels x n elements x TS lines), rounded up to an even count so
-// that the float2 FFT scratch after it is 8-byte aligned for odd n too
-__host__ __device__ constexpr int tile_floats(int n) { return (3 * n * TS + 1) & ~1; }
+// floats of a tile (one channel: n elements x TS lines), rounded up to an even count so that
+// the float2 FFT scratch after it is 8-byte aligned for odd n too
+__host__ __device__ constexpr int tile_floats(int n) { return (n * TS + 1) & ~1; }
 
 int sobolev_smem_bytes(int n) { return tile_floats(n) * 4 + SOB_WARPS * 2 * n * 8; }
 
@@ -161,8 +161,10 @@ __device__ __forceinline__ void divmod_n(int i, int n, int lg, int& q, int& rm) 
   rm = i - q * n;
 }
 
+// One pass over the tiles of the tile-path levels with nlo < n <= nhi (a size class, launched
+// with the shared memory of its largest level); tiles of the other class are skipped.
 template <int PASS>
-__global__ void __launch_bounds__(SOB_THREADS) k_sob(const Plan* __restrict__ P) {
+__global__ void __launch_bounds__(SOB_THREADS) k_sob(const Plan* __restrict__ P, int nlo, int nhi) {
   constexpr int AXIS = (PASS == 1 || PASS == 5) ? 0 : (PASS == 2 || PASS == 4) ? 1 : 2;
   extern __shared__ float smem[];
   const int nj = P->n_jobs;
@@ -180,30 +182,31 @@ __global__ void __launch_bounds__(SOB_THREADS) k_sob(const Plan* __restrict__ P)
       if (t < J.lev[l].tiles) break;
       t -= J.lev[l].tiles;
     }
-    if (l >= J.L) continue;
+    if (l >= J.L || J.lev[l].n <= nlo || J.lev[l].n > nhi) continue;
     const Level& lv = J.lev[l];
     const int n = lv.n, lg = lv.lg, n3 = lv.n3, nl = n * n;
-    const int r0 = t * TILE_LINES;
+    // a tile: TILE_LINES lines of one channel (channel-major over the level's tiles)
+    const int lt = (nl + TILE_LINES - 1) / TILE_LINES;
+    const int c = t / lt;
+    const int r0 = (t - c * lt) * TILE_LINES;
     float* tl = smem;
     float2* b0 = reinterpret_cast<float2*>(smem + tile_floats(n)) + warp * 2 * n;
     float2* b1 = b0 + n;
-    const float* src = (PASS == 1 || (PASS == 5 && !pre)) ? lv.g : lv.tmp;
+    const float* src = ((PASS == 1 || (PASS == 5 && !pre)) ? lv.g : lv.tmp) + (size_t)c * n3;
 
-    for (int idx = threadIdx.x; idx < 3 * TILE_LINES * n; idx += SOB_THREADS) {
-      const int c = idx / (TILE_LINES * n);
-      const int rem = idx - c * TILE_LINES * n;
+    for (int idx = threadIdx.x; idx < TILE_LINES * n; idx += SOB_THREADS) {
       int tt, e;
-      if (AXIS == 0) divmod_n(rem, n, lg, tt, e);
-      else { e = rem >> 5; tt = rem & 31; }
+      if (AXIS == 0) divmod_n(idx, n, lg, tt, e);
+      else { e = idx >> 5; tt = idx & 31; }
       const int r = r0 + tt;
-      tl[(c * n + e) * TS + tt] = r < nl ? src[(size_t)c * n3 + eaddr<AXIS>(n, lg, r, e)] : 0.f;
+      tl[e * TS + tt] = r < nl ? src[eaddr<AXIS>(n, lg, r, e)] : 0.f;
     }
     __syncthreads();
 
     if (n > 1 && pre) {
-      for (int pp = warp; pp < 3 * TILE_LINES / 2; pp += SOB_WARPS) {
-        const int c = pp / (TILE_LINES / 2), tt = (pp % (TILE_LINES / 2)) * 2;
-        float* A = tl + c * n * TS + tt;
+      for (int pp = warp; pp < TILE_LINES / 2; pp += SOB_WARPS) {
+        const int tt = pp * 2;
+        float* A = tl + tt;
         float* B = A + 1;
         if (PASS == 1 || PASS == 2 || PASS == 3) dct2_pair(A, B, n, b0, b1, lv.tw, lv.tw4, lane);
         if (PASS == 3) {
@@ -232,44 +235,42 @@ __global__ void __launch_bounds__(SOB_THREADS) k_sob(const Plan* __restrict__ P)
     __syncthreads();
 
     if (PASS < 5) {
-      for (int idx = threadIdx.x; idx < 3 * TILE_LINES * n; idx += SOB_THREADS) {
-        const int c = idx / (TILE_LINES * n);
-        const int rem = idx - c * TILE_LINES * n;
+      float* dst = lv.tmp + (size_t)c * n3;
+      for (int idx = threadIdx.x; idx < TILE_LINES * n; idx += SOB_THREADS) {
         int tt, e;
-        if (AXIS == 0) divmod_n(rem, n, lg, tt, e);
-        else { e = rem >> 5; tt = rem & 31; }
+        if (AXIS == 0) divmod_n(idx, n, lg, tt, e);
+        else { e = idx >> 5; tt = idx & 31; }
         const int r = r0 + tt;
-        if (r < nl) lv.tmp[(size_t)c * n3 + eaddr<AXIS>(n, lg, r, e)] = tl[(c * n + e) * TS + tt];
+        if (r < nl) dst[eaddr<AXIS>(n, lg, r, e)] = tl[e * TS + tt];
       }
     } else {
-      // Adam (PyTorch semantics) on the vertices of these x-lines
+      // Adam (PyTorch semantics) on channel c of the vertices of these x-lines (the other
+      // channels' tiles write the other components of theta: disjoint 4-byte words)
       const float b1f = J.beta1, b2f = J.beta2;
       const float step = lv.lr * J.bias[0];
       const float ib2 = J.bias[1];
+      float* tmpc = lv.tmp + (size_t)c * n3;
+      float* mc = lv.m + (size_t)c * n3;
+      float* vc = lv.v + (size_t)c * n3;
       for (int idx = threadIdx.x; idx < TILE_LINES * n; idx += SOB_THREADS) {
         int tt, x;
         divmod_n(idx, n, lg, tt, x);
         const int r = r0 + tt;
         if (r >= nl) continue;
         const int v = r * n + x;
-        float4 th = lv.theta[v];
-        float* thc = &th.x;
-#pragma unroll
+        const float g = tl[x * TS + tt];
         if (J.no_adam) {
-          for (int c = 0; c < 3; ++c) lv.tmp[(size_t)c * n3 + v] = tl[(c * n + x) * TS + tt];
+          tmpc[v] = g;
           continue;
         }
-        for (int c = 0; c < 3; ++c) {
-          const float g = tl[(c * n + x) * TS + tt];
-          if (J.keep_pgrad) lv.tmp[(size_t)c * n3 + v] = g;
-          float m = lv.m[(size_t)c * n3 + v], vv = lv.v[(size_t)c * n3 + v];
-          m = b1f * m + (1.f - b1f) * g;
-          vv = b2f * vv + (1.f - b2f) * g * g;
-          lv.m[(size_t)c * n3 + v] = m;
-          lv.v[(size_t)c * n3 + v] = vv;
-          thc[c] -= step * m / (sqrtf(vv) * ib2 + J.eps);
-        }
-        lv.theta[v] = th;
+        if (J.keep_pgrad) tmpc[v] = g;
+        float m = mc[v], vv = vc[v];
+        m = b1f * m + (1.f - b1f) * g;
+        vv = b2f * vv + (1.f - b2f) * g * g;
+        mc[v] = m;
+        vc[v] = vv;
+        float* th = reinterpret_cast<float*>(lv.theta + v) + c;
+        *th -= step * m / (sqrtf(vv) * ib2 + J.eps);
       }
     }
     __syncthreads();
@@ -285,13 +286,16 @@ void sobolev_configure() {
   cudaFuncSetAttribute(k_sob<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
-void launch_sobolev_tiles(const Plan* P, int grid, int nmax, cudaStream_t s) {
-  const int smem = sobolev_smem_bytes(nmax);
-  k_sob<1><<<grid, SOB_THREADS, smem, s>>>(P);
-  k_sob<2><<<grid, SOB_THREADS, smem, s>>>(P);
-  k_sob<3><<<grid, SOB_THREADS, smem, s>>>(P);
-  k_sob<4><<<grid, SOB_THREADS, smem, s>>>(P);
-  k_sob<5><<<grid, SOB_THREADS, smem, s>>>(P);
+// the five passes over the tile levels with nlo < n <= nhi; nsmem: the largest of them
+// (sets the shared memory per block and so the blocks per SM)
+void launch_sobolev_tiles(const Plan* P, int sms, int nlo, int nhi, int nsmem, cudaStream_t s) {
+  const int smem = sobolev_smem_bytes(nsmem);
+  const int grid = sms * std::max(1, std::min(8, (227 * 1024) / smem));
+  k_sob<1><<<grid, SOB_THREADS, smem, s>>>(P, nlo, nhi);
+  k_sob<2><<<grid, SOB_THREADS, smem, s>>>(P, nlo, nhi);
+  k_sob<3><<<grid, SOB_THREADS, smem, s>>>(P, nlo, nhi);
+  k_sob<4><<<grid, SOB_THREADS, smem, s>>>(P, nlo, nhi);
+  k_sob<5><<<grid, SOB_THREADS, smem, s>>>(P, nlo, nhi);
 }
 
 }  // namespace pdg

@@ -108,7 +108,7 @@ __global__ void k_static_setup(unsigned char* base, int n, int lg, float lam) {
     lv.n = n;
     lv.lg = lg;
     lv.n3 = n * n * n;
-    lv.tiles = (n * n + TILE_LINES - 1) / TILE_LINES;
+    lv.tiles = 3 * ((n * n + TILE_LINES - 1) / TILE_LINES);  // one channel per tile
     lv.lam = lam;
     lv.g = reinterpret_cast<float*>(base + SO_G);
     lv.tmp = reinterpret_cast<float*>(base + SO_TMP);

@@ -15,7 +15,7 @@ void launch_nn_hard(const Plan* P, int grid, cudaStream_t s, bool count);
 void launch_iso_edges(const Plan* P, int grid, cudaStream_t s);
 void launch_assemble(const Plan* P, int grid, cudaStream_t s);
 void launch_adjoint(const Plan* P, int grid, cudaStream_t s);
-void launch_sobolev_tiles(const Plan* P, int grid, int nmax, cudaStream_t s);
+void launch_sobolev_tiles(const Plan* P, int sms, int nlo, int nhi, int nsmem, cudaStream_t s);
 void launch_sobolev_plane(const Plan* P, int grid, int nmax, cudaStream_t s, int part = -1);
 void launch_loss(const Plan* P, int grid, cudaStream_t s);
 

@@ -42,7 +42,7 @@ struct Level {
   int n;       // vertices per axis (1 or a power of two)
   int lg;      // log2(n)
   int n3;      // n^3
-  int tiles;   // Sobolev tiles: ceil(n^2 / 32)
+  int tiles;   // tile-path Sobolev tiles: 3 channels x ceil(n^2 / 32) lines of 32
   float sc_hi[3], sc_lo[3];  // (n - 1) / (hi - lo) per axis as a float pair (hi + lo)
   float lr;    // learning rate of the level (already x0.1 without preconditioning)
   float lam;   // lambda of the level

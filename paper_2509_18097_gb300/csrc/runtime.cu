@@ -36,6 +36,26 @@ int grid_bits(long count, double per_cell = 8.0) {
   return std::min(std::max(b, 2), 7);
 }
 
+// Largest resolution of the levels the tile path preconditions, per size class (0: none).
+// Each class is launched with its own shared-memory size, so that small tile levels keep
+// several blocks per SM when a level above TILE_SPLIT shares the step (a batch).
+constexpr int TILE_SPLIT = 108;
+struct TileSizes {
+  int small = 0;  // tile levels of at most TILE_SPLIT vertices per axis
+  int big = 0;    // tile levels above TILE_SPLIT
+};
+TileSizes tile_sizes(int n) {
+  TileSizes t;
+  if (tile_level(n)) (n <= TILE_SPLIT ? t.small : t.big) = n;
+  return t;
+}
+TileSizes tmax(TileSizes a, TileSizes b) {
+  a.small = std::max(a.small, b.small);
+  a.big = std::max(a.big, b.big);
+  return a;
+}
+bool tgreater(TileSizes a, TileSizes b) { return a.small > b.small || a.big > b.big; }
+
 // 1, or 2..256 with no prime factor but 2 and 3 (the line transforms are radix-2/3 FFTs)
 bool valid_res(int n) {
   if (n < 1 || n > 256) return false;
@@ -98,7 +118,7 @@ struct pdg_ctx {
   float* stage = nullptr;  // [stage_pts][3] staging of host inputs
   int stage_pts = 0;
   int nmax = 1;
-  int ntile = 0;  // largest resolution among the levels the tile path preconditions (0: none)
+  TileSizes ntile;  // largest resolutions among the levels the tile path preconditions
   cudaStream_t cap = nullptr, cap2 = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int graph_kernels = 0;   // kernel nodes of gexec
@@ -127,7 +147,7 @@ struct pdg_batch {
   cudaStream_t cap = nullptr, cap2 = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int graph_nmax = 0;
-  int graph_ntile = 0;
+  TileSizes graph_ntile;
   bool dirty = true;  // membership changed since the last upload of the job table
   std::string err;
 };
@@ -318,13 +338,11 @@ enum StageIndex {
 // Stage i of a step; bump: the job_bump mode of the interpolation stage (1: optimisation
 // step, 2: evaluation); count: the nearest-neighbour instances that count candidates and
 // exact ties.  The plan's item prefixes must be current (refresh_plan).
-// nmax: the largest level resolution; ntile: the largest one of the levels the tile path
-// preconditions (0: none)
-void launch_stage(int i, const Plan* plan, int nmax, int ntile, int sms, cudaStream_t s, int bump = 1,
+// nmax: the largest level resolution; ntile: the largest ones of the levels the tile path
+// preconditions, per size class
+void launch_stage(int i, const Plan* plan, int nmax, TileSizes ntile, int sms, cudaStream_t s, int bump = 1,
                   bool count = false) {
   const int grid = sms * 8;
-  const int smem = sobolev_smem_bytes(std::max(ntile, 2));
-  const int tiles_per_sm = std::max(1, std::min(4, (227 * 1024) / std::max(smem, 1)));
   switch (i) {
     case S_INTERP: launch_interp(plan, grid, s, bump); break;
     case S_MOV_SCAN: launch_mov_scan(plan, sms * 2, s); break;
@@ -344,7 +362,8 @@ void launch_stage(int i, const Plan* plan, int nmax, int ntile, int sms, cudaStr
       break;
     }
     case S_SOB_256:
-      if (ntile > 0) launch_sobolev_tiles(plan, sms * tiles_per_sm, ntile, s);
+      if (ntile.small > 0) launch_sobolev_tiles(plan, sms, 0, TILE_SPLIT, ntile.small, s);
+      if (ntile.big > 0) launch_sobolev_tiles(plan, sms, TILE_SPLIT, 256, ntile.big, s);
       break;
     case S_LOSS: launch_loss(plan, sms * 2, s); break;
   }
@@ -354,7 +373,7 @@ constexpr int ST_SOB_FIRST = S_SOB_XY_FWD, ST_SOB_LAST = S_SOB_256;  // precondi
 // Captures one step.  Two branches: the isometry kernel runs beside the moving grid's sort
 // and the nearest-neighbour passes (it needs only the deformed points), the loss reduction
 // beside the adjoint and the preconditioner (nothing downstream reads it).
-pdg_status capture_step(pdg_ctx* c, const Plan* plan, int nmax, int ntile, cudaStream_t cap, cudaStream_t cap2,
+pdg_status capture_step(pdg_ctx* c, const Plan* plan, int nmax, TileSizes ntile, cudaStream_t cap, cudaStream_t cap2,
                         cudaGraphExec_t* out, std::string* err, int sms, int* n_kernels = nullptr) {
   cudaGraph_t g = nullptr;
   cudaEvent_t ev[4] = {};
@@ -583,7 +602,7 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
     lv.n = n;
     lv.lg = (n & (n - 1)) == 0 ? ilog2(n) : -1;
     lv.n3 = n * n * n;
-    lv.tiles = (n * n + TILE_LINES - 1) / TILE_LINES;
+    lv.tiles = 3 * ((n * n + TILE_LINES - 1) / TILE_LINES);  // one channel per tile
     lv.lr = (float)(cfg->lr0 * std::pow((double)cfg->lr_growth, l) * (cfg->precondition ? 1.0 : 0.1));
     lv.lam = (float)(cfg->lambda0 * std::pow((double)cfg->lambda_growth, l));
     for (int a = 0; a < 3; ++a) {
@@ -616,7 +635,7 @@ pdg_status pdg_create(const pdg_config* cfg, const float* template_xyz, int n_ve
     lv.n_active = (int*)P(o.n_active);
     lv.csum = (int*)P(o.csum);
     c->nmax = std::max(c->nmax, n);
-    if (tile_level(n)) c->ntile = std::max(c->ntile, n);
+    c->ntile = tmax(c->ntile, tile_sizes(n));
     mu.resize(n);
     tw.resize(n);
     tw4.resize(n);
@@ -1044,7 +1063,7 @@ pdg_status pdg_precondition(pdg_ctx* c, int level, const float* g, float* out, v
   CU(c, cudaMemcpyAsync(c->op_job, &oj, sizeof(Job), cudaMemcpyHostToDevice, s));
   CU(c, cudaMemcpyAsync(c->op_plan, &op, sizeof(Plan), cudaMemcpyHostToDevice, s));
   launch_plan(c->op_plan, s);
-  for (int i = ST_SOB_FIRST; i <= ST_SOB_LAST; ++i) launch_stage(i, c->op_plan, lv.n, tile_level(lv.n) ? lv.n : 0, c->sms, s);
+  for (int i = ST_SOB_FIRST; i <= ST_SOB_LAST; ++i) launch_stage(i, c->op_plan, lv.n, tile_sizes(lv.n), c->sms, s);
   launch_soa_to_aos(lv.tmp, tmp, lv.n3, s);
   CU(c, cudaGetLastError());
   const pdg_status st = copy_out(c, out, tmp, bytes, s);
@@ -1113,9 +1132,9 @@ pdg_status pdg_fit_mesh(pdg_ctx* c, const float* p0_xyz, int n_p0, int n_steps, 
   const int2* edges = J.edges;
   for (int k = 1; k <= n_steps; ++k) {
     launch_mesh_points(c->op_job, V, s);
-    for (int i = S_MOV_SCAN; i <= S_NN_HARD; ++i) launch_stage(i, c->op_plan, 1, 0, c->sms, s);
-    launch_stage(S_ASSEMBLE, c->op_plan, 1, 0, c->sms, s);
-    launch_stage(S_LOSS, c->op_plan, 1, 0, c->sms, s);
+    for (int i = S_MOV_SCAN; i <= S_NN_HARD; ++i) launch_stage(i, c->op_plan, 1, TileSizes(), c->sms, s);
+    launch_stage(S_ASSEMBLE, c->op_plan, 1, TileSizes(), c->sms, s);
+    launch_stage(S_LOSS, c->op_plan, 1, TileSizes(), c->sms, s);
     // (I + lambda L)^{-2} dL/dX by two solves, then Adam on the vertices
     launch_mesh_solve(J.v2e_ptr, J.v2e, edges, J.gy, h, r, d0, d1, V, lambda, (float)emax, iters, s);
     launch_mesh_solve(J.v2e_ptr, J.v2e, edges, h, pg, r, d0, d1, V, lambda, (float)emax, iters, s);
@@ -1197,14 +1216,15 @@ pdg_status pdg_batch_step(pdg_batch* b, int n_steps, void* cuda_stream) {
   if (!b || n_steps < 0) return PDG_ERR_INVALID;
   if (b->n == 0 || n_steps == 0) return PDG_OK;
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  int nmax = 1, ntile = 0, sms = 1;
+  int nmax = 1, sms = 1;
+  TileSizes ntile;
   for (auto* c : b->members) {
     if (!c->in_frame) {
       b->err = "batch member outside a frame";
       return PDG_ERR_STATE;
     }
     nmax = std::max(nmax, c->nmax);
-    ntile = std::max(ntile, c->ntile);
+    ntile = tmax(ntile, c->ntile);
     sms = c->sms;
   }
   if (b->dirty) {
@@ -1228,14 +1248,14 @@ pdg_status pdg_batch_step(pdg_batch* b, int n_steps, void* cuda_stream) {
     b->gens.resize(b->members.size());
     for (size_t i = 0; i < b->members.size(); ++i) b->gens[i] = b->members[i]->frame_gen;
   }
-  if (!b->gexec || nmax > b->graph_nmax || ntile > b->graph_ntile) {
+  if (!b->gexec || nmax > b->graph_nmax || tgreater(ntile, b->graph_ntile)) {
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;
     if (cudaStreamSynchronize(s) != cudaSuccess) return PDG_ERR_CUDA;
-    const pdg_status st = capture_step(nullptr, b->dplan, std::max(nmax, b->graph_nmax), std::max(ntile, b->graph_ntile), b->cap, b->cap2, &b->gexec, &b->err, sms);
+    const pdg_status st = capture_step(nullptr, b->dplan, std::max(nmax, b->graph_nmax), tmax(ntile, b->graph_ntile), b->cap, b->cap2, &b->gexec, &b->err, sms);
     if (st != PDG_OK) return st;
     b->graph_nmax = std::max(nmax, b->graph_nmax);
-    b->graph_ntile = std::max(ntile, b->graph_ntile);
+    b->graph_ntile = tmax(ntile, b->graph_ntile);
   }
   for (int i = 0; i < n_steps; ++i)
     if (cudaGraphLaunch(b->gexec, s) != cudaSuccess) return PDG_ERR_CUDA;
