@@ -99,3 +99,24 @@ def test_create_rejects_bad_arguments_without_touching_a_gpu(lib):
     bad = binding.pdg_config_default(res=(0,))
     st = lib.pdg_create(C.byref(bad), None, 10, None, 0, None, 5, 5, None, C.byref(out))
     assert st == binding.ERR_INVALID
+
+
+def test_batched_workload_sizes_are_accepted(lib):
+    """The batched / served workload draws its levels as 2^a 3^b sizes: each is one the
+    library accepts, the finest lies in the drawn range, and levels do not shrink toward the finest."""
+    from paper_2509_18097_gb300 import binding, synth
+
+    assert synth.smooth23(181) == 192 and synth.smooth23(100) == 96 and synth.smooth23(13.5) == 12
+    for m in synth.SMOOTH_SIZES:
+        k = m
+        while k % 2 == 0:
+            k //= 2
+        while k % 3 == 0:
+            k //= 3
+        assert k == 1 and 2 <= m <= 256
+    for i in range(40):
+        res = synth.batched_job(i)["res"]
+        assert 27 <= res[-1] <= 256 and all(r >= 4 for r in res)
+        assert all(a <= b for a, b in zip(res, res[1:])), res  # the floor of 4 may repeat
+        cfg = binding.pdg_config_default(res=res)
+        assert binding.pdg_query_bytes(cfg, 10, 10, 10) > 0, res
