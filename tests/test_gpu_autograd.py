@@ -225,7 +225,7 @@ def test_grid_loss_function_vs_finite_differences_and_oracle():
     ref = O.interp_adjoint(x, g_pts, cfg.res, cfg.lo, cfg.hi)
     terms = O.interp_adjoint(x, np.abs(g_pts), cfg.res, cfg.lo, cfg.hi)
     loss_ref = cfg.w_chamfer_mesh * cm["loss"] + cfg.w_chamfer_pts * cp["loss"] + cfg.w_iso * iso
-    assert abs(float(loss) - loss_ref) <= 1e-5 * abs(loss_ref)
+    assert abs(float(loss.detach()) - loss_ref) <= 1e-5 * abs(loss_ref)
     near = np.zeros(V + N, bool)  # points matched through a near-tie are left out of (1)
     for lo, hi in ((0, V), (V, V + N)):
         idx, d2 = O.nn_exact(y_gpu[lo:hi], P)
